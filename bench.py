@@ -1,0 +1,366 @@
+"""Benchmark: batched OMP signals/s on one GB300 (or N replicas under torchrun).
+
+A step is one whole solve (every OMP iteration: correlate, select, append, update, compact,
+finalize) of the batch through the C ABI, graph-replayed, with the dictionary prepared and the
+signals resident in HBM before the timed region. Workload: the 1024 x 8192 Gaussian dictionary,
+B = 4096 planted 32-sparse signals with noise sigma = 1e-3, S = 32 fixed iterations. The chosen
+form (BF16 tensor-core correlation with FP32 top-8 rescoring) is timed next to the plain FP32
+path on the same GPU; the L2 is flushed (a 512 MiB write) between timed steps.
+
+Roofline: the dominant kernel's per-launch duration comes from CUDA events recorded around
+every correlation / update launch inside an instrumented replay of the same graph
+(omp_profile_*); algorithmic FLOPs / bytes per launch are derived from the live counts.
+
+``--impl reference`` times the FP64 CPU oracle (timed mode) on the host cores instead, each step
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import gen  # noqa: E402
+
+WORKLOAD = "gaussian_1024x8192_s32_b4096"
+METRIC = "OMP signals/s, chosen form vs plain FP32 on same GB300 at matched support; % roofline"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts)
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def time_oracle(w, A, Y, seconds_target=15.0, max_signals=None):
+    """FP64 timed-mode oracle on a bounded sample: grows the sample until ~seconds_target."""
+    from oracle import omp as oracle_omp
+    n = 16
+    total_t, total_n = 0.0, 0
+    while True:
+        rows = slice(0, min(n, Y.shape[0]))
+        t0 = time.perf_counter()
+        oracle_omp.omp_batch(A, Y[rows], w.S, w.eps, True)
+        dt = time.perf_counter() - t0
+        total_t, total_n = dt, rows.stop
+        if total_t >= seconds_target / 4 or rows.stop >= Y.shape[0] or \
+                (max_signals and rows.stop >= max_signals):
+            break
+        n *= 2
+    return total_n / total_t, total_n, total_t
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2407_06434_gb300 import omp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = gen.get_config(args.config)
+    A = gen.dictionary(w)
+    Y, *_ = gen.signals(w, A)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+    Yd = torch.from_numpy(Y).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def bench_form(prec):
+        solver = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
+        h = solver.h
+        X = torch.empty((w.B, w.S), dtype=torch.float32, device=dev)
+        sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
+        omp.omp_prepare_dictionary(h, Ad)
+        for _ in range(args.warmup):
+            omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        total = sum(ms)
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        # instrumented replay: per-launch durations of correlation and update kernels
+        omp.omp_profile_enable(h, True)
+        corr = np.zeros(w.S)
+        upd = np.zeros(w.S)
+        live = None
+        for i in range(max(1, min(args.steps, 5))):
+            flush.zero_()
+            omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
+            c, u, lv = omp.omp_profile_read(h, w.S)
+            corr += c
+            upd += u
+            live = lv
+            n_prof = i + 1
+        omp.omp_profile_enable(h, False)
+        corr /= n_prof
+        upd /= n_prof
+        # end to end through the host entry point (pinned buffers, copies inside)
+        Yh = torch.from_numpy(Y).pin_memory()
+        Xh = torch.empty((w.B, w.S), dtype=torch.float32).pin_memory()
+        Sh = torch.empty((w.B, w.S), dtype=torch.int32).pin_memory()
+        omp.omp_solve_batch_host(h, Ad, Yh, w.S, w.eps, Xh, Sh)
+        e2e_t = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            omp.omp_solve_batch_host(h, Ad, Yh, w.S, w.eps, Xh, Sh)
+            e2e_t.append(time.perf_counter() - t0)
+        res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live,
+                   e2e_s=float(np.sum(e2e_t)), e2e_steps=len(e2e_t),
+                   sup=sup.cpu().numpy(), X=X.cpu().numpy())
+        solver.close()
+        return res
+
+    with Clocks(local) as clk:
+        chosen = bench_form(args.precision)
+    plain = bench_form("fp32") if args.precision != "fp32" and not args.skip_plain else None
+    clocks = clk.summary()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = load_peaks()
+    B_all = w.B * world
+    value = B_all * args.steps / (chosen["total_ms"] / 1e3)
+    # roofline: dominant kernel of the chosen form
+    live = chosen["live"].astype(np.float64)
+    corr_ms, upd_ms = chosen["corr"], chosen["upd"]
+    flops_corr = 2.0 * w.M * w.N * live                    # per launch
+    k = np.arange(w.S)
+    qbytes = 4 if args.precision == "fp32" else 0
+    topk = 1 if args.precision == "fp32" else 8
+    # update: gather of k+1 FP32 atom rows + topk FP32 rescoring rows (quantised paths)
+    # + residual read and write, per live signal
+    upd_bytes = live * 4.0 * w.M * ((k + 1) + (topk if topk > 1 else 0) + 2)
+    if corr_ms.sum() >= upd_ms.sum():
+        dur = corr_ms.mean() / 1e3
+        achieved = float(flops_corr.mean() / dur / 1e12)
+        if args.precision == "fp32":
+            peak, unit, bound, src = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu", "nominal"
+        else:
+            key = "bf16_tflops_sustained"
+            peak = peaks.get(key, PEAKS_FALLBACK[key]) * (2.0 if args.precision == "fp8" else 1.0)
+            unit, bound, src = "TFLOP/s", "tensor", peak_src
+        kern = "correlate"
+        alg = float(flops_corr.mean())
+    else:
+        dur = upd_ms.mean() / 1e3
+        achieved = float(upd_bytes.mean() / dur / 1e9)
+        peak, unit, bound, src = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]), "GB/s", "hbm", \
+            peak_src
+        kern = "update"
+        alg = float(upd_bytes.mean())
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel": kern,
+                "peak_source": src, "algorithmic_per_launch": alg,
+                "launch_ms": float(dur * 1e3),
+                "corr_ms_per_step": float(corr_ms.sum()), "update_ms_per_step": float(upd_ms.sum())}
+    e2e_value = B_all * chosen["e2e_steps"] / chosen["e2e_s"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "signals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": chosen["total_ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8_e4m3"}[args.precision],
+        "data": "synthetic (seeded Gaussian dictionary and planted sparse signals)",
+        "config": {"workload": w.name, "M": w.M, "N": w.N, "B": w.B, "S": w.S,
+                   "precision": args.precision, "rescore_topk": topk,
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "signals/s",
+                "h2d_bytes_per_step": int(w.B * w.M * 4),
+                "d2h_bytes_per_step": int(w.B * w.S * 8)},
+        "gpu_launches": int(args.steps * (3 * w.S + 3)),
+        "roofline": roofline,
+    }
+    if plain is not None:
+        pv = B_all * args.steps / (plain["total_ms"] / 1e3)
+        same = float(np.mean(np.all(plain["sup"] == chosen["sup"], axis=1)))
+        line["plain_fp32"] = {"value": pv, "ms_per_step": plain["total_ms"] / args.steps,
+                              "corr_ms_per_step": float(plain["corr"].sum()),
+                              "update_ms_per_step": float(plain["upd"].sum()),
+                              "support_match_rate": same}
+        line["speedup_vs_plain_fp32"] = value / pv
+    if not args.no_cpu_baseline:
+        v, n, t = time_oracle(w, A, Y, seconds_target=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "signals/s", "cores": oracle_cores(),
+                                "kind": "oracle",
+                                "sample": f"first {n} signals of the batch, FP64 timed-mode "
+                                          f"oracle, {t:.1f} s"}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import omp as oracle_omp
+    w = gen.get_config(args.config)
+    A = gen.dictionary(w)
+    n = args.reference_signals
+    Y, *_ = gen.signals(w, A, rows=slice(0, n))
+    for _ in range(args.warmup):
+        oracle_omp.omp_batch(A, Y, w.S, w.eps, True)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_omp.omp_batch(A, Y, w.S, w.eps, True)
+        t.append(time.perf_counter() - t0)
+    value = n * args.steps / sum(t)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "signals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(t) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "M": w.M, "N": w.N, "B": w.B, "S": w.S,
+                   "sample_signals_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "signals/s", "cores": oracle_cores(),
+                         "kind": "oracle",
+                         "sample": f"first {n} signals of the batch per step, FP64 timed-mode "
+                                   "oracle"},
+        "e2e": {"value": value, "unit": "signals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-signals", type=int, default=64)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

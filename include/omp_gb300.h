@@ -1,0 +1,154 @@
+/*
+ * omp_gb300.h -- batched Orthogonal Matching Pursuit on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is Alg. 1 of "A Practical GPU-Accelerated Implementation of Orthogonal Matching
+ * Pursuit" (arXiv 2407.06434): for k = 1..S pick n* = argmax_n |<r_{k-1}, a_n>| / ||a_n||, add
+ * n* to the support, solve least squares on the support and set r_k = y - A_S x_k; stop when
+ * ||r_k|| <= eps. The least squares step uses the inverse-Cholesky recurrence of Sec. 2.3
+ * (F_k = V_k^{-T}, gamma = 1/sqrt(||a||^2 - ||z||^2)) with A^T a_{n*} read from the Gram matrix
+ * (Sec. 2.2), and the projection y_hat = A_k F_k (A_k F_k)^T y, so each iteration updates the
+ * residual by one orthonormal direction q_k = A_k F_k[:, k].
+ *
+ * Conventions shared by every entry point:
+ *  - Layout. A is M x N column-major (lda = M): atom n is the M contiguous floats at A + n*M.
+ *    Signals are rows: Y and R are B x M row-major. Per-signal outputs are B x S row-major.
+ *  - Pointers. Every pointer is a DEVICE pointer on the handle's device unless the name ends in
+ *    _host. Device pointers must be 16-byte aligned. The caller owns all of its buffers; the
+ *    handle owns its workspaces and the prepared copies of the dictionary.
+ *  - Streams. `stream` is a cudaStream_t (0 = the legacy default stream). Work is enqueued on it
+ *    and the call returns without waiting, except the *_host entry point and omp_get_error.
+ *  - Errors. Argument errors are returned synchronously and nothing is enqueued. A CUDA launch
+ *    failure returns OMP_ERR_CUDA. Errors detected on the device (a bounded wait that ran out, a
+ *    non-finite input) set a sticky error word that omp_get_error reads. No exception crosses
+ *    this interface and there is no CPU fallback: a handle can only be created on an sm_103
+ *    device.
+ *  - Threads. One handle per host thread at a time; distinct handles are independent.
+ *  - Ties. Wherever scores tie exactly, the smallest atom index wins.
+ */
+#ifndef OMP_GB300_H
+#define OMP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct omp_handle_s* omp_handle;
+
+typedef enum {
+  OMP_OK = 0,
+  OMP_ERR_INVALID_ARGUMENT = 1,   /* bad pointer, size, alignment or option */
+  OMP_ERR_UNSUPPORTED_DEVICE = 2, /* not a compute capability 10.3 device */
+  OMP_ERR_OUT_OF_MEMORY = 3,      /* a workspace allocation failed */
+  OMP_ERR_CUDA = 4,               /* a CUDA runtime call failed */
+  OMP_ERR_DEVICE_TIMEOUT = 5,     /* a bounded device-side wait ran out (see omp_get_error) */
+  OMP_ERR_NUMERICAL = 6           /* a signal had non-finite entries (it was returned empty) */
+} omp_status;
+
+typedef enum {
+  OMP_PREC_FP32 = 0,     /* correlation A^T R in FP32 on the CUDA cores, fused top-1 */
+  OMP_PREC_BF16 = 1,     /* BF16 tensor-core correlation, FP32 accumulate, top-8 rescored in FP32 */
+  OMP_PREC_FP8_E4M3 = 2  /* E4M3 tensor-core correlation with per-atom and per-signal scales,
+                            FP32 accumulate, top-8 rescored in FP32 */
+} omp_precision;
+
+/* Device error word bits (omp_get_error). */
+#define OMP_DEVERR_WAIT_TIMEOUT 0x1  /* a bounded mbarrier / flag wait gave up */
+#define OMP_DEVERR_NONFINITE 0x2     /* a signal contained NaN or Inf */
+#define OMP_DEVERR_BAD_STATE 0x4     /* an internal index was out of range (skipped) */
+
+typedef struct omp_desc {
+  int64_t M;             /* signal length (rows of A), 1 <= M <= 16384 */
+  int64_t N;             /* number of atoms (columns of A), 2 <= N <= 65536 */
+  int64_t max_batch;     /* largest B any solve on this handle will pass, >= 1 */
+  int32_t max_iters;     /* largest S any solve will pass, 1 <= max_iters <= min(M, N, 256) */
+  int32_t precision;     /* omp_precision */
+  int32_t rescore_topk;  /* quantised paths: candidates rescored in FP32, 1..8 (0 means 8) */
+  int32_t eps_relative;  /* 1: stop when ||r_k|| <= eps * ||y||; 0: when ||r_k|| <= eps (Alg. 1) */
+  int32_t use_graph;     /* 1: capture each (B, S, eps) solve once as a CUDA graph and replay it */
+  int32_t device;        /* CUDA device ordinal the handle lives on */
+} omp_desc;
+
+/* Fill `desc` with defaults for an M x N dictionary (precision BF16, rescore_topk 8,
+ * eps_relative 1, use_graph 1, device 0, max_batch 4096, max_iters min(M, N, 64)). */
+void omp_desc_default(omp_desc* desc, int64_t M, int64_t N);
+
+/* Create a handle: checks the device (sm_103 only), allocates every workspace for max_batch and
+ * max_iters (including the N x N FP32 Gram matrix), and returns it in *out. No dictionary is
+ * prepared yet. Returns OMP_ERR_UNSUPPORTED_DEVICE on any other device, OMP_ERR_OUT_OF_MEMORY if
+ * an allocation fails (nothing is leaked). */
+omp_status omp_create(const omp_desc* desc, omp_handle* out);
+
+/* Release every resource of the handle (synchronises its device first). NULL is accepted. */
+omp_status omp_destroy(omp_handle h);
+
+/* Prepare the dictionary A (device, M x N column-major): column norms in FP64 (the 1/||a_n|| of
+ * Alg. 1's score), a zero-padded FP32 copy, the BF16 or E4M3 copy with per-atom scales for the
+ * tensor-core path, and the Gram matrix G = A^T A in FP32 (Sec. 2.2). Solves call this
+ * implicitly when A differs from the last prepared pointer; the contents of A must not change
+ * under the same pointer unless this function is called again. */
+omp_status omp_prepare_dictionary(omp_handle h, const float* A, void* stream);
+
+/* Solve B independent OMP problems with the shared dictionary A (Alg. 1).
+ *   A            device, M x N column-major (prepared if it is not the cached pointer)
+ *   Y            device, B x M row-major measurements
+ *   B            1 <= B <= max_batch; S: 1 <= S <= max_iters; eps >= 0 (see eps_relative)
+ *   X_out        device, B x S float: coefficients in selection order, in the scale of the
+ *                caller's A (App. A), 0 past the signal's last iteration
+ *   support_out  device, B x S int32: atom indices in selection order, -1 past the last one
+ * A signal stops after S iterations, when ||r_k|| <= eps (relative or absolute), when the picked
+ * atom is linearly dependent on its support (||a||^2 - ||z||^2 <= 1e-10 ||a||^2; the atom is not
+ * added), or at once when y = 0 (empty support). */
+omp_status omp_solve_batch(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                           float eps, float* X_out, int32_t* support_out, void* stream);
+
+/* omp_solve_batch plus per-signal diagnostics (each pointer may be NULL):
+ *   n_iter_out      device, B int32: iterations performed (= number of support entries)
+ *   resid_norm_out  device, B float: final ||r|| as tracked by the update (FP32 residual)
+ *   stop_out        device, B int32: 0 = S reached, 1 = eps, 2 = dependent atom, 3 = y == 0 or
+ *                   non-finite input */
+omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                              float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                              float* resid_norm_out, int32_t* stop_out, void* stream);
+
+/* End-to-end variant with HOST buffers for the signals and results: copies Y_host (B x M) to
+ * the device, solves, copies X_host (B x S) and support_host (B x S) back and waits for the
+ * stream. Pinned host memory makes the copies asynchronous DMA; pageable memory works but is
+ * slower. A stays a prepared device dictionary. */
+omp_status omp_solve_batch_host(omp_handle h, const float* A, const float* Y_host, int64_t B,
+                                int32_t S, float eps, float* X_host, int32_t* support_host,
+                                void* stream);
+
+/* One correlate-and-select step (Alg. 1's argmax) for B residuals R (device, B x M): the
+ * handle's correlation path scores every atom, s_n = |<r, a_n>| / ||a_n|| (quantised paths:
+ * |<q(r), q(a_n)>| times the atom's scale / ||a_n||, r's own scale omitted since it does not
+ * change the order), and writes the `topk` best per signal in decreasing score, ties to the
+ * lower index:  idx_out (device, B x topk int32) and score_out (device, B x topk float).
+ * topk is 1 for OMP_PREC_FP32 and rescore_topk otherwise. No FP32 rescoring is applied here. */
+omp_status omp_correlate_topk(omp_handle h, const float* A, const float* R, int64_t B,
+                              int32_t topk, int32_t* idx_out, float* score_out, void* stream);
+
+/* Per-launch timing. When enabled, the next solves record CUDA events around every correlation
+ * and update launch (a separate captured graph with event-record nodes; results are the same
+ * as without it). omp_profile_read synchronises `stream` and returns, for the most recent
+ * solve, each iteration's correlation and update launch duration in milliseconds
+ * (corr_ms, update_ms: S floats each, device-independent host arrays) and the live signal count
+ * at the start of each iteration (live_out: S int32, may be NULL). S must equal that solve's S.
+ * Returns OMP_ERR_INVALID_ARGUMENT if profiling was off for that solve. */
+omp_status omp_profile_enable(omp_handle h, int32_t enable);
+omp_status omp_profile_read(omp_handle h, int32_t S, float* corr_ms_host, float* update_ms_host,
+                            int32_t* live_host, void* stream);
+
+/* Read and clear the device error word (OMP_DEVERR_* bits); synchronises the handle's work on
+ * `stream` first. Returns OMP_ERR_DEVICE_TIMEOUT if the timeout bit was set, OMP_ERR_NUMERICAL
+ * if only the non-finite bit was set, else OMP_OK. */
+omp_status omp_get_error(omp_handle h, int32_t* flags, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* omp_status_string(omp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OMP_GB300_H */

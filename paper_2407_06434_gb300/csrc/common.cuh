@@ -1,0 +1,161 @@
+// Internal definitions shared by the kernels and the host runtime of the batched OMP library.
+//
+// Data layout in HBM (one handle):
+//   dictionary (prepared once per A):
+//     A32   N x Mp  float   atom rows, zero padded to Mp (multiple of 64)   -- update / rescoring
+//     A16   N x Mp  bf16    RN-even copy                                     -- BF16 correlation
+//     A8    N x Mp  e4m3    per-atom scaled copy, sa[n] = amax_n / 448        -- FP8 correlation
+//     inv_norm[N] float = 1/||a_n|| (from FP64), norm2[N] double = ||a_n||^2
+//     gram  N x N   float   G = A^T A (Sec. 2.2 precompute)
+//   per signal, indexed by the signal id b (its row in Y):
+//     R32   Bmax x Mp float  residual r (the master copy)
+//     F     Bmax x Smax(Smax+1)/2 double  packed upper-triangular inverse Cholesky factor,
+//           column j holds F[0..j, j] at offset j(j+1)/2 (Sec. 2.3)
+//     bv    Bmax x Smax double  b_j = q_j^T r_{j-1} (so x = F b)
+//     sup   Bmax x Smax int     support in selection order
+//     ynorm, rnorm (float), niter, stop (int)
+//   per live position p (the compacted order of the signals still iterating):
+//     live[2][Bmax]  position -> signal id, ping-pong by iteration parity
+//     cnt[Smax+2]    cnt[j+1] = live count after compaction j (cnt[0] = B)
+//     flag[Bmax]     1 if the signal at position p continues after this iteration
+//     Rq[2]          Bpad x Mp quantised residual rows in position order (tensor-core operand)
+//     sr[2][Bpad]    per-position FP8 scale of Rq
+//     cand1[Bmax]    FP32 path: packed (score, ~index) key, merged with atomicMax
+//     cand_s/cand_i  quantised paths: per position, candidate pieces x 8 (score, index)
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/omp_gb300.h"
+
+namespace ompk {
+
+constexpr int kMpAlign = 64;          // M padding: one 128-byte row of a BF16 K-chunk
+constexpr int kSigTile = 128;         // signals per correlation tile (TMEM lanes)
+constexpr int kMaxTopk = 8;
+constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a||^2
+constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
+
+struct Ws {
+  int M, Mp, N, Smax, Bmax, Bpad;
+  int prec;        // omp_precision
+  int topk;        // candidates kept per signal by the correlation (1 for FP32)
+  int pieces;      // candidate pieces per position (quantised paths)
+  int64_t Fstride; // Smax (Smax + 1) / 2
+  // dictionary
+  float* A32;
+  __nv_bfloat16* A16;
+  uint8_t* A8;
+  float* sa;
+  float* inv_norm;
+  double* norm2;
+  float* gram;
+  // signal state
+  float* R32;
+  void* Rq[2];
+  float* sr[2];
+  int* live[2];
+  int* cnt;
+  uint8_t* flag;
+  unsigned long long* cand1;
+  float* cand_s;
+  int* cand_i;
+  double* F;
+  double* bv;
+  int* sup;
+  float* ynorm;
+  float* rnorm;
+  int* niter;
+  int* stop;
+  unsigned int* err;
+};
+
+// Per-call user pointers, written to device memory by a one-thread kernel before each solve so
+// that a captured graph stays valid for any caller buffers.
+struct CallArgs {
+  const float* Y;
+  float* X;
+  int* support;
+  int* n_iter;
+  float* resid;
+  int* stop;
+  int* topk_idx;     // omp_correlate_topk outputs
+  float* topk_score;
+};
+
+__device__ __forceinline__ unsigned long long pack_key(float score, int idx) {
+  // scores are >= 0, so their IEEE bits order like unsigned integers; the low word is
+  // ~idx so that on equal scores the smaller index gives the larger key
+  return (static_cast<unsigned long long>(__float_as_uint(score)) << 32) |
+         static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<unsigned>(idx));
+}
+__device__ __forceinline__ int key_index(unsigned long long key) {
+  return static_cast<int>(0xFFFFFFFFu - static_cast<unsigned>(key & 0xFFFFFFFFull));
+}
+__device__ __forceinline__ float key_score(unsigned long long key) {
+  return __uint_as_float(static_cast<unsigned>(key >> 32));
+}
+// (s, i) beats (t, j): higher score, or equal score and lower index
+__device__ __forceinline__ bool better(float s, int i, float t, int j) {
+  return s > t || (s == t && i < j);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over a 256-thread block; `red` holds >= 9 doubles of shared memory. All threads return
+// the total. Contains __syncthreads (every thread of the block must call it).
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < 8 ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[8] = t;
+  }
+  __syncthreads();
+  const double out = red[8];
+  __syncthreads();
+  return out;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).
+void launch_prep(const Ws& ws, const float* A, cudaStream_t s);
+void launch_gram_simt(const Ws& ws, cudaStream_t s);
+void launch_corr_simt(const Ws& ws, int k, int B, cudaStream_t s);
+void launch_init(const Ws& ws, const CallArgs* args, int B, cudaStream_t s);
+void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s);
+void launch_compact(const Ws& ws, int j, int B, cudaStream_t s);
+void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
+void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStream_t s);
+void launch_topk_out(const Ws& ws, const CallArgs* args, int B, int topk, cudaStream_t s);
+void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s);
+size_t update_smem_bytes(const Ws& ws);
+cudaError_t configure_update_kernels(const Ws& ws);
+
+// tensor-core correlation (corr_tc.cu)
+struct TcPlan;
+int tc_pieces(int Mp, int N, int Bpad, int sm_count);
+cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan);
+void tc_destroy(TcPlan* plan);
+void launch_corr_tc(const Ws& ws, const TcPlan* plan, int k, int B, cudaStream_t s);
+
+}  // namespace ompk

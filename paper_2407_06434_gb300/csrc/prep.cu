@@ -1,0 +1,49 @@
+// Dictionary preparation (once per A): FP64 column norms (the ||a_n|| of Alg. 1's score, App. A),
+// the zero-padded FP32 atom rows used by the update, and the quantised copies used by the
+// tensor-core correlation (BF16 round-to-nearest-even; E4M3 with a per-atom scale
+// amax_n / 448, satfinite round-to-nearest-even).
+#include "common.cuh"
+
+namespace ompk {
+
+// One warp per atom; grid-stride over atoms. Reads column n of the caller's A (M contiguous
+// floats at A + n*M) with coalesced scalar loads, so any M and any 4-byte alignment works.
+__global__ void __launch_bounds__(256) prep_kernel(Ws ws, const float* __restrict__ A) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; n < ws.N; n += warps) {
+    const float* a = A + static_cast<size_t>(n) * ws.M;
+    float* a32 = ws.A32 + static_cast<size_t>(n) * ws.Mp;
+    double s = 0.0;
+    float amax = 0.f;
+    for (int m = lane; m < ws.Mp; m += 32) {
+      const float v = m < ws.M ? a[m] : 0.f;
+      a32[m] = v;
+      s += static_cast<double>(v) * static_cast<double>(v);
+      amax = fmaxf(amax, fabsf(v));
+    }
+    s = warp_sum(s);
+    amax = warp_max(amax);
+    if (lane == 0) {
+      ws.norm2[n] = s;
+      ws.inv_norm[n] = s > 0.0 ? static_cast<float>(1.0 / sqrt(s)) : 0.f;
+    }
+    if (ws.prec == OMP_PREC_BF16) {
+      __nv_bfloat16* a16 = ws.A16 + static_cast<size_t>(n) * ws.Mp;
+      for (int m = lane; m < ws.Mp; m += 32) a16[m] = __float2bfloat16_rn(a32[m]);
+    } else if (ws.prec == OMP_PREC_FP8_E4M3) {
+      const float inv = amax > 0.f ? 448.f / amax : 0.f;
+      if (lane == 0) ws.sa[n] = amax > 0.f ? amax / 448.f : 0.f;
+      uint8_t* a8 = ws.A8 + static_cast<size_t>(n) * ws.Mp;
+      for (int m = lane; m < ws.Mp; m += 32)
+        a8[m] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(a32[m] * inv, __NV_SATFINITE, __NV_E4M3));
+    }
+  }
+}
+
+void launch_prep(const Ws& ws, const float* A, cudaStream_t s) {
+  const int blocks = (ws.N + 7) / 8;
+  prep_kernel<<<blocks < 65535 ? blocks : 65535, 256, 0, s>>>(ws, A);
+}
+
+}  // namespace ompk

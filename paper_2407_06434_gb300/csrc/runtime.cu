@@ -1,0 +1,444 @@
+// Host runtime behind the C ABI of include/omp_gb300.h: handle and workspace management,
+// dictionary preparation, the per-iteration launch sequence, CUDA-graph capture and replay.
+//
+// One solve is: set_args, init, compaction 0, then for k = 0..S-1 {correlate(k), update(k),
+// compaction(k+1)}, then finalize. Every kernel reads the live count of its iteration from
+// device memory and returns at once past it, so the whole sequence is launch-invariant: it is
+// captured once per (B, S, eps) into a CUDA graph and replayed with one cudaGraphLaunch, the
+// per-call pointers travelling through a small device-side argument block.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace ompk;
+
+struct GraphEntry {
+  int B, S;
+  float eps;
+  int prof;  // 1 if captured with profiling event nodes
+  cudaGraphExec_t exec;
+};
+
+struct omp_handle_s {
+  omp_desc d{};
+  int dev = 0;
+  int sm_count = 0;
+  Ws ws{};
+  TcPlan* tc = nullptr;
+  const float* prepared_A = nullptr;
+  CallArgs* args_dev = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphEntry> graphs;
+  std::vector<void*> allocs;
+  float* y_stage = nullptr;
+  float* x_stage = nullptr;
+  int* s_stage = nullptr;
+  // profiling: events[(kind * Smax + k) * 2 + {0: start, 1: end}], kind 0 = correlate, 1 = update
+  bool prof_on = false;
+  int prof_last_S = 0;
+  bool prof_last_valid = false;
+  std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool fault_alloc_due() {
+  // test hook: OMP_FAULT_ALLOC_AT=n makes the n-th workspace allocation of a handle fail
+  static int counter = 0;
+  const char* v = std::getenv("OMP_FAULT_ALLOC_AT");
+  if (!v) return false;
+  const int at = std::atoi(v);
+  return at > 0 && ++counter == at;
+}
+
+template <class T>
+bool dalloc(omp_handle_s* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return true;
+  if (fault_alloc_due()) return false;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+void release(omp_handle_s* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  h->prof_ev.clear();
+  if (h->tc) tc_destroy(h->tc);
+  h->tc = nullptr;
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+omp_status check_launch() {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
+}
+
+void enqueue_correlate(omp_handle_s* h, int k, int B, cudaStream_t s) {
+  if (h->ws.prec == OMP_PREC_FP32)
+    launch_corr_simt(h->ws, k, B, s);
+  else
+    launch_corr_tc(h->ws, h->tc, k, B, s);
+}
+
+void prof_mark(omp_handle_s* h, bool prof, int kind, int k, int end, cudaStream_t s) {
+  if (!prof) return;
+  cudaEventRecordWithFlags(h->prof_ev[(static_cast<size_t>(kind) * h->ws.Smax + k) * 2 + end], s,
+                           cudaEventRecordExternal);
+}
+
+void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStream_t s) {
+  const Ws& ws = h->ws;
+  launch_init(ws, h->args_dev, B, s);
+  launch_compact(ws, 0, B, s);
+  for (int k = 0; k < S; ++k) {
+    prof_mark(h, prof, 0, k, 0, s);
+    enqueue_correlate(h, k, B, s);
+    prof_mark(h, prof, 0, k, 1, s);
+    prof_mark(h, prof, 1, k, 0, s);
+    launch_update(ws, k, B, S, eps, h->d.eps_relative, s);
+    prof_mark(h, prof, 1, k, 1, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, B, s);
+  }
+  launch_finalize(ws, h->args_dev, B, S, s);
+}
+
+void enqueue_topk(omp_handle_s* h, const float* R, int B, int topk, cudaStream_t s) {
+  launch_load_rows(h->ws, R, B, s);
+  launch_compact(h->ws, 0, B, s);
+  enqueue_correlate(h, 0, B, s);
+  launch_topk_out(h->ws, h->args_dev, B, topk, s);
+}
+
+omp_status prepare(omp_handle_s* h, const float* A, cudaStream_t s) {
+  launch_prep(h->ws, A, s);
+  launch_gram_simt(h->ws, s);
+  const omp_status st = check_launch();
+  if (st == OMP_OK) h->prepared_A = A;
+  return st;
+}
+
+omp_status run_solve(omp_handle_s* h, int B, int S, float eps, cudaStream_t stream) {
+  const bool prof = h->prof_on;
+  h->prof_last_S = S;
+  h->prof_last_valid = prof;
+  if (!h->d.use_graph) {
+    enqueue_solve(h, B, S, eps, prof, stream);
+    return check_launch();
+  }
+  for (auto& g : h->graphs)
+    if (g.prof == static_cast<int>(prof) && g.B == B && g.S == S && g.eps == eps)
+      return cudaGraphLaunch(g.exec, stream) == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
+  // capture on the handle's own stream (capture only records; the replay below runs in the
+  // caller's stream order)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    enqueue_solve(h, B, S, eps, prof, h->cap_stream);
+    ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    return OMP_ERR_CUDA;
+  }
+  h->graphs.push_back(GraphEntry{B, S, eps, static_cast<int>(prof), exec});
+  return cudaGraphLaunch(exec, stream) == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
+}
+
+omp_status validate_solve(omp_handle_s* h, const float* A, const float* Y, int64_t B, int32_t S,
+                          float eps, const void* X, const void* sup) {
+  if (!h || !A || !Y || !X || !sup) return OMP_ERR_INVALID_ARGUMENT;
+  if (B < 1 || B > h->d.max_batch) return OMP_ERR_INVALID_ARGUMENT;
+  if (S < 1 || S > h->d.max_iters) return OMP_ERR_INVALID_ARGUMENT;
+  if (!(eps >= 0.f) || !std::isfinite(eps)) return OMP_ERR_INVALID_ARGUMENT;
+  if (!aligned16(A) || !aligned16(Y) || !aligned16(X) || !aligned16(sup))
+    return OMP_ERR_INVALID_ARGUMENT;
+  return OMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void omp_desc_default(omp_desc* d, int64_t M, int64_t N) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->M = M;
+  d->N = N;
+  d->max_batch = 4096;
+  int64_t s = M < N ? M : N;
+  d->max_iters = static_cast<int32_t>(s < 64 ? s : 64);
+  d->precision = OMP_PREC_BF16;
+  d->rescore_topk = 8;
+  d->eps_relative = 1;
+  d->use_graph = 1;
+  d->device = 0;
+}
+
+const char* omp_status_string(omp_status s) {
+  switch (s) {
+    case OMP_OK: return "OMP_OK";
+    case OMP_ERR_INVALID_ARGUMENT: return "OMP_ERR_INVALID_ARGUMENT";
+    case OMP_ERR_UNSUPPORTED_DEVICE: return "OMP_ERR_UNSUPPORTED_DEVICE";
+    case OMP_ERR_OUT_OF_MEMORY: return "OMP_ERR_OUT_OF_MEMORY";
+    case OMP_ERR_CUDA: return "OMP_ERR_CUDA";
+    case OMP_ERR_DEVICE_TIMEOUT: return "OMP_ERR_DEVICE_TIMEOUT";
+    case OMP_ERR_NUMERICAL: return "OMP_ERR_NUMERICAL";
+  }
+  return "OMP_ERR_UNKNOWN";
+}
+
+omp_status omp_create(const omp_desc* desc, omp_handle* out) {
+  if (!desc || !out) return OMP_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  const omp_desc d = *desc;
+  if (d.M < 1 || d.M > 16384 || d.N < 2 || d.N > 65536 || d.max_batch < 1 ||
+      d.max_batch > (1 << 24) || d.max_iters < 1 || d.max_iters > 256 || d.max_iters > d.M ||
+      d.max_iters > d.N || d.precision < 0 || d.precision > 2 || d.rescore_topk < 0 ||
+      d.rescore_topk > kMaxTopk)
+    return OMP_ERR_INVALID_ARGUMENT;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || d.device < 0 || d.device >= ndev) {
+    cudaGetLastError();
+    return OMP_ERR_UNSUPPORTED_DEVICE;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, d.device) != cudaSuccess) return OMP_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return OMP_ERR_UNSUPPORTED_DEVICE;
+  DeviceGuard guard(d.device);
+
+  omp_handle_s* h = new (std::nothrow) omp_handle_s();
+  if (!h) return OMP_ERR_OUT_OF_MEMORY;
+  h->d = d;
+  if (h->d.rescore_topk == 0) h->d.rescore_topk = kMaxTopk;
+  h->dev = d.device;
+  h->sm_count = prop.multiProcessorCount;
+  Ws& ws = h->ws;
+  ws.M = static_cast<int>(d.M);
+  ws.Mp = static_cast<int>((d.M + kMpAlign - 1) / kMpAlign * kMpAlign);
+  ws.N = static_cast<int>(d.N);
+  ws.Smax = d.max_iters;
+  ws.Bmax = static_cast<int>(d.max_batch);
+  ws.Bpad = (ws.Bmax + kSigTile - 1) / kSigTile * kSigTile;
+  ws.prec = d.precision;
+  ws.topk = d.precision == OMP_PREC_FP32 ? 1 : h->d.rescore_topk;
+  ws.Fstride = static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2;
+  ws.pieces = d.precision == OMP_PREC_FP32 ? 0 : tc_pieces(ws.Mp, ws.N, ws.Bpad, h->sm_count);
+  const size_t N = ws.N, Mp = ws.Mp, Bm = ws.Bmax, Bp = ws.Bpad, Sm = ws.Smax;
+  const size_t qbytes = d.precision == OMP_PREC_BF16 ? 2 : 1;
+  bool ok = true;
+  ok = ok && dalloc(h, &ws.A32, N * Mp);
+  if (d.precision == OMP_PREC_BF16) ok = ok && dalloc(h, &ws.A16, N * Mp);
+  if (d.precision == OMP_PREC_FP8_E4M3) ok = ok && dalloc(h, &ws.A8, N * Mp) && dalloc(h, &ws.sa, N);
+  ok = ok && dalloc(h, &ws.inv_norm, N) && dalloc(h, &ws.norm2, N) && dalloc(h, &ws.gram, N * N);
+  ok = ok && dalloc(h, &ws.R32, Bm * Mp);
+  if (d.precision != OMP_PREC_FP32) {
+    uint8_t* q0 = nullptr;
+    uint8_t* q1 = nullptr;
+    ok = ok && dalloc(h, &q0, Bp * Mp * qbytes) && dalloc(h, &q1, Bp * Mp * qbytes);
+    ws.Rq[0] = q0;
+    ws.Rq[1] = q1;
+    ok = ok && dalloc(h, &ws.sr[0], Bp) && dalloc(h, &ws.sr[1], Bp);
+    ok = ok && dalloc(h, &ws.cand_s, Bp * ws.pieces * kMaxTopk) &&
+         dalloc(h, &ws.cand_i, Bp * ws.pieces * kMaxTopk);
+  }
+  ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
+  ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
+  ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
+       dalloc(h, &ws.sup, Bm * Sm);
+  ok = ok && dalloc(h, &ws.ynorm, Bm) && dalloc(h, &ws.rnorm, Bm) && dalloc(h, &ws.niter, Bm) &&
+       dalloc(h, &ws.stop, Bm) && dalloc(h, &ws.err, 1) && dalloc(h, &h->args_dev, 1);
+  ok = ok && dalloc(h, &h->y_stage, Bm * static_cast<size_t>(ws.M)) &&
+       dalloc(h, &h->x_stage, Bm * Sm) && dalloc(h, &h->s_stage, Bm * Sm);
+  if (!ok) {
+    release(h);
+    delete h;
+    return OMP_ERR_OUT_OF_MEMORY;
+  }
+  bool cuda_ok = cudaMemset(ws.err, 0, sizeof(unsigned)) == cudaSuccess &&
+                 cudaMemset(ws.cand1, 0, Bm * sizeof(unsigned long long)) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 configure_update_kernels(ws) == cudaSuccess;
+  if (cuda_ok && d.precision != OMP_PREC_FP32) cuda_ok = tc_setup(ws, h->sm_count, &h->tc) == cudaSuccess;
+  if (cuda_ok) cuda_ok = cudaDeviceSynchronize() == cudaSuccess;
+  if (!cuda_ok) {
+    cudaGetLastError();
+    release(h);
+    delete h;
+    return OMP_ERR_CUDA;
+  }
+  *out = h;
+  return OMP_OK;
+}
+
+omp_status omp_destroy(omp_handle h) {
+  if (!h) return OMP_OK;
+  {
+    DeviceGuard guard(h->dev);
+    cudaDeviceSynchronize();
+    release(h);
+  }
+  delete h;
+  return OMP_OK;
+}
+
+omp_status omp_prepare_dictionary(omp_handle h, const float* A, void* stream) {
+  if (!h || !A || !aligned16(A)) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  return prepare(h, A, static_cast<cudaStream_t>(stream));
+}
+
+omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                              float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                              float* resid_norm_out, int32_t* stop_out, void* stream) {
+  omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
+  if (st != OMP_OK) return st;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A != h->prepared_A) {
+    st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+  }
+  CallArgs a{};
+  a.Y = Y;
+  a.X = X_out;
+  a.support = support_out;
+  a.n_iter = n_iter_out;
+  a.resid = resid_norm_out;
+  a.stop = stop_out;
+  launch_set_args(h->args_dev, a, s);
+  st = check_launch();
+  if (st != OMP_OK) return st;
+  return run_solve(h, static_cast<int>(B), S, eps, s);
+}
+
+omp_status omp_solve_batch(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                           float eps, float* X_out, int32_t* support_out, void* stream) {
+  return omp_solve_batch_ex(h, A, Y, B, S, eps, X_out, support_out, nullptr, nullptr, nullptr,
+                            stream);
+}
+
+omp_status omp_solve_batch_host(omp_handle h, const float* A, const float* Y_host, int64_t B,
+                                int32_t S, float eps, float* X_host, int32_t* support_host,
+                                void* stream) {
+  if (!h || !Y_host || !X_host || !support_host) return OMP_ERR_INVALID_ARGUMENT;
+  if (B < 1 || B > h->d.max_batch || S < 1 || S > h->d.max_iters) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ybytes = static_cast<size_t>(B) * h->ws.M * sizeof(float);
+  if (cudaMemcpyAsync(h->y_stage, Y_host, ybytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OMP_ERR_CUDA;
+  omp_status st = omp_solve_batch_ex(h, A, h->y_stage, B, S, eps, h->x_stage, h->s_stage, nullptr,
+                                     nullptr, nullptr, stream);
+  if (st != OMP_OK) return st;
+  const size_t obytes = static_cast<size_t>(B) * S * sizeof(float);
+  if (cudaMemcpyAsync(X_host, h->x_stage, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(support_host, h->s_stage, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return OMP_ERR_CUDA;
+  return OMP_OK;
+}
+
+omp_status omp_correlate_topk(omp_handle h, const float* A, const float* R, int64_t B,
+                              int32_t topk, int32_t* idx_out, float* score_out, void* stream) {
+  if (!h || !A || !R || !idx_out || !score_out) return OMP_ERR_INVALID_ARGUMENT;
+  if (B < 1 || B > h->d.max_batch) return OMP_ERR_INVALID_ARGUMENT;
+  const int want = h->ws.prec == OMP_PREC_FP32 ? 1 : h->ws.topk;
+  if (topk != want) return OMP_ERR_INVALID_ARGUMENT;
+  if (!aligned16(A) || !aligned16(R)) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A != h->prepared_A) {
+    const omp_status st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+  }
+  CallArgs a{};
+  a.topk_idx = idx_out;
+  a.topk_score = score_out;
+  launch_set_args(h->args_dev, a, s);
+  enqueue_topk(h, R, static_cast<int>(B), topk, s);
+  return check_launch();
+}
+
+omp_status omp_profile_enable(omp_handle h, int32_t enable) {
+  if (!h) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  if (enable && h->prof_ev.empty()) {
+    const size_t n = static_cast<size_t>(h->ws.Smax) * 4;
+    h->prof_ev.resize(n, nullptr);
+    for (size_t i = 0; i < n; ++i)
+      if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) return OMP_ERR_CUDA;
+  }
+  h->prof_on = enable != 0;
+  return OMP_OK;
+}
+
+omp_status omp_profile_read(omp_handle h, int32_t S, float* corr_ms_host, float* update_ms_host,
+                            int32_t* live_host, void* stream) {
+  if (!h || !corr_ms_host || !update_ms_host) return OMP_ERR_INVALID_ARGUMENT;
+  if (!h->prof_last_valid || S != h->prof_last_S) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return OMP_ERR_CUDA;
+  for (int kind = 0; kind < 2; ++kind)
+    for (int k = 0; k < S; ++k) {
+      const size_t i = (static_cast<size_t>(kind) * h->ws.Smax + k) * 2;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->prof_ev[i], h->prof_ev[i + 1]) != cudaSuccess) return OMP_ERR_CUDA;
+      (kind == 0 ? corr_ms_host : update_ms_host)[k] = ms;
+    }
+  if (live_host) {
+    if (cudaMemcpy(live_host, h->ws.cnt + 1, sizeof(int) * S, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OMP_ERR_CUDA;
+  }
+  return OMP_OK;
+}
+
+omp_status omp_get_error(omp_handle h, int32_t* flags, void* stream) {
+  if (!h) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned v = 0;
+  if (cudaMemcpyAsync(&v, h->ws.err, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(h->ws.err, 0, sizeof(unsigned), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return OMP_ERR_CUDA;
+  if (flags) *flags = static_cast<int32_t>(v);
+  if (v & OMP_DEVERR_WAIT_TIMEOUT) return OMP_ERR_DEVICE_TIMEOUT;
+  if (v & OMP_DEVERR_NONFINITE) return OMP_ERR_NUMERICAL;
+  return OMP_OK;
+}
+
+}  // extern "C"

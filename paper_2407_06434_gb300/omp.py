@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in include/omp_gb300.h (argument marshalling only).
+
+The functions carry the C names and take torch CUDA tensors; every computation runs in
+``libomp_gb300.so``. There is no fallback: if the library is missing or the GPU is not an sm_103
+device, the calls raise.
+
+Tensor conventions (same as the C ABI):
+  A            (M, N) float32 in column-major storage, i.e. ``A.stride() == (1, M)``
+               (``At.t()`` for a contiguous (N, M) ``At``, or ``torch.from_numpy`` of a Fortran
+               array)
+  Y / R        (B, M) float32, contiguous
+  X_out        (B, S) float32, support_out (B, S) int32
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from .build import LIB
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp8_e4m3": 2}
+STATUS = {0: "OMP_OK", 1: "OMP_ERR_INVALID_ARGUMENT", 2: "OMP_ERR_UNSUPPORTED_DEVICE",
+          3: "OMP_ERR_OUT_OF_MEMORY", 4: "OMP_ERR_CUDA", 5: "OMP_ERR_DEVICE_TIMEOUT",
+          6: "OMP_ERR_NUMERICAL"}
+DEVERR_WAIT_TIMEOUT, DEVERR_NONFINITE, DEVERR_BAD_STATE = 0x1, 0x2, 0x4
+STOP_ITERS, STOP_EPS, STOP_DEPENDENT, STOP_ZERO = 0, 1, 2, 3
+
+# every symbol include/omp_gb300.h declares
+EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_dictionary",
+           "omp_solve_batch", "omp_solve_batch_ex", "omp_solve_batch_host", "omp_correlate_topk",
+           "omp_get_error", "omp_status_string", "omp_profile_enable", "omp_profile_read"]
+
+
+class omp_desc(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("max_batch", ctypes.c_int64),
+                ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("rescore_topk", ctypes.c_int32), ("eps_relative", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class OmpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64, _I32, _F32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "omp_desc_default": (None, [ctypes.POINTER(omp_desc), _I64, _I64]),
+        "omp_create": (_I32, [ctypes.POINTER(omp_desc), ctypes.POINTER(_P)]),
+        "omp_destroy": (_I32, [_P]),
+        "omp_prepare_dictionary": (_I32, [_P, _P, _P]),
+        "omp_solve_batch": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P]),
+        "omp_solve_batch_ex": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
+        "omp_solve_batch_host": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P]),
+        "omp_correlate_topk": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P]),
+        "omp_get_error": (_I32, [_P, ctypes.POINTER(_I32), _P]),
+        "omp_status_string": (ctypes.c_char_p, [_I32]),
+        "omp_profile_enable": (_I32, [_P, _I32]),
+        "omp_profile_read": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise OmpError(st, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_A(A, M, N):
+    if A.dtype.is_floating_point is False or str(A.dtype) != "torch.float32":
+        raise ValueError("A must be float32")
+    if tuple(A.shape) != (M, N) or A.stride() != (1, M):
+        raise ValueError(f"A must be an ({M}, {N}) column-major tensor (stride (1, {M}))")
+
+
+def omp_desc_default(M: int, N: int) -> omp_desc:
+    d = omp_desc()
+    load().omp_desc_default(ctypes.byref(d), M, N)
+    return d
+
+
+class Handle:
+    """An ``omp_handle`` plus the descriptor it was created with."""
+
+    def __init__(self, ptr: ctypes.c_void_p, desc: omp_desc):
+        self.ptr = ptr
+        self.desc = desc
+
+    @property
+    def M(self):
+        return self.desc.M
+
+    @property
+    def N(self):
+        return self.desc.N
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.omp_destroy(self.ptr)
+            self.ptr = None
+
+
+def omp_create(M: int, N: int, max_batch: int = 4096, max_iters: int = 64,
+               precision: str = "bf16", rescore_topk: int = 8, eps_relative: bool = True,
+               use_graph: bool = True, device: int = 0) -> Handle:
+    lib = load()
+    d = omp_desc()
+    lib.omp_desc_default(ctypes.byref(d), M, N)
+    d.max_batch, d.max_iters = max_batch, max_iters
+    d.precision = PRECISIONS[precision]
+    d.rescore_topk, d.eps_relative = rescore_topk, int(eps_relative)
+    d.use_graph, d.device = int(use_graph), device
+    h = ctypes.c_void_p()
+    _check(lib.omp_create(ctypes.byref(d), ctypes.byref(h)), "omp_create")
+    return Handle(h, d)
+
+
+def omp_destroy(h: Handle):
+    if h.ptr:
+        _check(load().omp_destroy(h.ptr), "omp_destroy")
+        h.ptr = None
+
+
+def omp_prepare_dictionary(h: Handle, A, stream=None):
+    _check_A(A, h.M, h.N)
+    _check(load().omp_prepare_dictionary(h.ptr, _ptr(A), _stream(stream)),
+           "omp_prepare_dictionary")
+
+
+def omp_solve_batch(h: Handle, A, Y, S: int, eps: float, X_out, support_out, stream=None):
+    _check_A(A, h.M, h.N)
+    B = Y.shape[0]
+    _check(load().omp_solve_batch(h.ptr, _ptr(A), _ptr(Y), B, S, eps, _ptr(X_out),
+                                  _ptr(support_out), _stream(stream)), "omp_solve_batch")
+
+
+def omp_solve_batch_ex(h: Handle, A, Y, S: int, eps: float, X_out, support_out, n_iter_out=None,
+                       resid_norm_out=None, stop_out=None, stream=None):
+    _check_A(A, h.M, h.N)
+    B = Y.shape[0]
+    _check(load().omp_solve_batch_ex(h.ptr, _ptr(A), _ptr(Y), B, S, eps, _ptr(X_out),
+                                     _ptr(support_out), _ptr(n_iter_out), _ptr(resid_norm_out),
+                                     _ptr(stop_out), _stream(stream)), "omp_solve_batch_ex")
+
+
+def omp_solve_batch_host(h: Handle, A, Y_host, S: int, eps: float, X_host, support_host,
+                         stream=None):
+    """Y_host, X_host, support_host: CPU tensors (pinned for asynchronous copies)."""
+    _check_A(A, h.M, h.N)
+    B = Y_host.shape[0]
+    _check(load().omp_solve_batch_host(h.ptr, _ptr(A), _ptr(Y_host), B, S, eps, _ptr(X_host),
+                                       _ptr(support_host), _stream(stream)),
+           "omp_solve_batch_host")
+
+
+def omp_correlate_topk(h: Handle, A, R, topk: int, idx_out, score_out, stream=None):
+    _check_A(A, h.M, h.N)
+    _check(load().omp_correlate_topk(h.ptr, _ptr(A), _ptr(R), R.shape[0], topk, _ptr(idx_out),
+                                     _ptr(score_out), _stream(stream)), "omp_correlate_topk")
+
+
+def omp_get_error(h: Handle, stream=None):
+    """Returns (status, flags) and clears the device error word."""
+    flags = _I32(0)
+    st = load().omp_get_error(h.ptr, ctypes.byref(flags), _stream(stream))
+    return st, flags.value
+
+
+def omp_profile_enable(h: Handle, enable: bool = True):
+    _check(load().omp_profile_enable(h.ptr, int(enable)), "omp_profile_enable")
+
+
+def omp_profile_read(h: Handle, S: int, stream=None):
+    """Per-iteration (correlation ms, update ms, live count) of the last profiled solve."""
+    import numpy as np
+    corr = np.zeros(S, dtype=np.float32)
+    upd = np.zeros(S, dtype=np.float32)
+    live = np.zeros(S, dtype=np.int32)
+    _check(load().omp_profile_read(h.ptr, S, corr.ctypes.data_as(_P), upd.ctypes.data_as(_P),
+                                   live.ctypes.data_as(_P), _stream(stream)), "omp_profile_read")
+    return corr, upd, live
+
+
+def omp_status_string(status: int) -> str:
+    return load().omp_status_string(status).decode()
+
+
+class OmpSolver:
+    """Convenience wrapper: owns a handle and allocates the outputs of each solve."""
+
+    def __init__(self, M, N, max_batch=4096, max_iters=64, precision="bf16", **kw):
+        self.h = omp_create(M, N, max_batch, max_iters, precision, **kw)
+
+    def solve(self, A, Y, S, eps=0.0, stream=None, diagnostics=False):
+        import torch
+        B = Y.shape[0]
+        X = torch.empty((B, S), dtype=torch.float32, device=Y.device)
+        sup = torch.empty((B, S), dtype=torch.int32, device=Y.device)
+        if not diagnostics:
+            omp_solve_batch(self.h, A, Y, S, eps, X, sup, stream)
+            return X, sup
+        n_iter = torch.empty(B, dtype=torch.int32, device=Y.device)
+        resid = torch.empty(B, dtype=torch.float32, device=Y.device)
+        stop = torch.empty(B, dtype=torch.int32, device=Y.device)
+        omp_solve_batch_ex(self.h, A, Y, S, eps, X, sup, n_iter, resid, stop, stream)
+        return X, sup, n_iter, resid, stop
+
+    def close(self):
+        omp_destroy(self.h)

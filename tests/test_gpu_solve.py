@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes: the hand-worked fixtures; the 64 x 256 planted workload in full; ragged shapes that span
+several correlation tiles with a partial last tile in M, N and B; eps-stopped uneven batches;
+the full-size 1024 x 8192, B = 4096, S = 32 workload checked on sampled signals; edge cases
+(zero and non-finite signals, dependent atoms, exact ties across tiles)."""
+import numpy as np
+import pytest
+
+from oracle import omp as oracle
+from tests import golden_util, parity
+from workloads import gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PRECS = ["fp32"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_06434_gb300 import build
+    build.build()
+    from paper_2407_06434_gb300 import omp
+    omp.load()
+    return omp
+
+
+def dev_dict(A):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float32).T)).cuda().t()
+
+
+def solve(prec, A, Y, S, eps=0.0, eps_relative=True, use_graph=True, max_batch=None, topk=8):
+    from paper_2407_06434_gb300 import omp
+    M, N = A.shape
+    B = Y.shape[0]
+    s = omp.OmpSolver(M, N, max_batch=max_batch or B, max_iters=S, precision=prec,
+                      eps_relative=eps_relative, use_graph=use_graph, rescore_topk=topk)
+    Ad = dev_dict(A)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).cuda()
+    X, sup, n_iter, resid, stop = s.solve(Ad, Yd, S, eps, diagnostics=True)
+    torch.cuda.synchronize()
+    out = dict(X=X.cpu().numpy(), sup=sup.cpu().numpy(), n_iter=n_iter.cpu().numpy(),
+               resid=resid.cpu().numpy(), stop=stop.cpu().numpy())
+    out["status"] = omp.omp_get_error(s.h)
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", golden_util.FIXTURES)
+def test_golden_fixtures(prec, name):
+    d = golden_util.load(name)
+    A = d["A"].astype(np.float32)
+    r = solve(prec, A, d["y"][None, :].astype(np.float32), d["S"])
+    k = d["n_iter"]
+    assert r["n_iter"][0] == k
+    assert list(r["sup"][0, :k]) == d["support"]
+    assert np.all(r["sup"][0, k:] == -1)
+    np.testing.assert_allclose(r["X"][0, :k], d["coef"], rtol=1e-5, atol=1e-6)
+    if d.get("stop") == "dependent":
+        assert r["stop"][0] == oracle.STOP_DEPENDENT
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_planted_64x256_full(prec):
+    w = gen.get_config("gaussian_64x256_s8_b16")
+    A = gen.dictionary(w)
+    Y, sp, sup, coef = gen.signals(w, A)
+    ref = oracle.omp_batch(A, Y, w.S)
+    r = solve(prec, A, Y, w.S)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"])
+    assert st["tie_diverged"] == 0
+    assert np.array_equal(r["sup"], ref.support)
+    assert all(set(r["sup"][b]) == set(sup[b]) for b in range(w.B))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_tiles(prec):
+    """M = 200 (padded to 256), N = 1000 (7 full atom tiles + a partial one), B = 300 (two full
+    signal tiles + a partial one), S = 24, noisy."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=200, N=1000, B=300, S=24, s_min=5, s_max=24,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=3)
+    Y, *_ = gen.signals(w, A, seed=3)
+    ref = oracle.omp_batch(A, Y, w.S)
+    r = solve(prec, A, Y, w.S)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"])
+    assert st["tie_diverged"] <= 3, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("eps_relative", [True, False])
+def test_eps_stop_uneven(prec, eps_relative):
+    """Per-signal sparsity 4..40 with a low noise floor: the eps stop fires near k = s, so the
+    live set shrinks unevenly and is compacted every iteration."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=2048, B=200, S=48, s_min=4, s_max=40,
+                       sigma=1e-6, col_scale=1.0)
+    A = gen.dictionary(w, seed=4)
+    Y, sp, _, _ = gen.signals(w, A, seed=4)
+    eps = 1e-3 if eps_relative else 5e-3
+    ref = oracle.omp_batch(A, Y, w.S, eps, eps_relative)
+    r = solve(prec, A, Y, w.S, eps=eps, eps_relative=eps_relative)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"], eps=eps,
+                        eps_relative=eps_relative)
+    assert np.mean(r["n_iter"] < w.S) > 0.9
+    assert np.mean(r["stop"] == oracle.STOP_EPS) > 0.9
+    assert st["tie_diverged"] <= 2, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_zero_and_nonfinite_signals(prec):
+    w = gen.get_config("gaussian_64x256_s8_b16", B=20)
+    A = gen.dictionary(w)
+    Y, *_ = gen.signals(w, A)
+    Y[3] = 0.0
+    Y[7, 5] = np.nan
+    Y[11, 0] = np.inf
+    good = [b for b in range(w.B) if b not in (3, 7, 11)]
+    ref = oracle.omp_batch(A, Y[good], w.S)
+    r = solve(prec, A, Y, w.S)
+    for b in (3, 7, 11):
+        assert r["n_iter"][b] == 0 and np.all(r["sup"][b] == -1) and np.all(r["X"][b] == 0)
+        assert r["stop"][b] == oracle.STOP_ZERO
+    status, flags = r["status"]
+    assert status == 6 and flags & 0x2
+    parity.compare(A, Y[good], ref, r["sup"][good], r["X"][good], r["n_iter"][good],
+                   r["resid"][good])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_graph_replay_and_direct_launches_agree(prec):
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", M=128, N=512, B=100, S=16, s_min=16, s_max=16,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=6)
+    Y, *_ = gen.signals(w, A, seed=6)
+    Ad = dev_dict(A)
+    Yd = torch.from_numpy(Y).cuda()
+    outs = []
+    for use_graph in (True, False):
+        s = omp.OmpSolver(w.M, w.N, max_batch=128, max_iters=16, precision=prec,
+                          use_graph=use_graph)
+        for _ in range(2):     # second call replays the captured graph
+            X, sup = s.solve(Ad, Yd, w.S)
+            outs.append((X.cpu().numpy(), sup.cpu().numpy()))
+        s.close()
+    for X, sup in outs[1:]:
+        assert np.array_equal(sup, outs[0][1])
+        assert np.array_equal(X.view(np.uint32), outs[0][0].view(np.uint32))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_entry_point(prec):
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", B=64)
+    A = gen.dictionary(w)
+    Y, *_ = gen.signals(w, A)
+    s = omp.OmpSolver(w.M, w.N, max_batch=64, max_iters=8, precision=prec)
+    Ad = dev_dict(A)
+    Xd, supd = s.solve(Ad, torch.from_numpy(Y).cuda(), 8)
+    Yh = torch.from_numpy(Y).pin_memory()
+    Xh = torch.empty((64, 8), dtype=torch.float32).pin_memory()
+    Sh = torch.empty((64, 8), dtype=torch.int32).pin_memory()
+    omp.omp_solve_batch_host(s.h, Ad, Yh, 8, 0.0, Xh, Sh)
+    assert np.array_equal(Sh.numpy(), supd.cpu().numpy())
+    assert np.array_equal(Xh.numpy(), Xd.cpu().numpy())
+    s.close()
+
+
+def test_correlate_top1_fp32_and_ties_across_tiles():
+    """FP32 correlation: the top-1 atom equals the FP64 argmax wherever the FP64 top-two margin
+    exceeds 1e-5; exact ties made by duplicated columns (in another atom tile and another
+    signal tile) resolve to the lower index."""
+    from paper_2407_06434_gb300 import omp
+    rng = np.random.default_rng(8)
+    M, N, B = 96, 700, 260
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    A[:, 650] = A[:, 37]          # duplicate in another atom tile
+    A[:, 300] = A[:, 299]         # duplicate in the same tile
+    A = np.asfortranarray(A)
+    R = rng.standard_normal((B, M)).astype(np.float32)
+    R[5] = A[:, 37] * 2.0         # signal 5's best atoms are 37 and 650 (exact tie)
+    R[200] = -A[:, 300]           # signal 200 ties 299 and 300
+    s = omp.OmpSolver(M, N, max_batch=B, max_iters=1, precision="fp32")
+    idx = torch.empty((B, 1), dtype=torch.int32, device="cuda")
+    sc = torch.empty((B, 1), dtype=torch.float32, device="cuda")
+    omp.omp_correlate_topk(s.h, dev_dict(A), torch.from_numpy(R).cuda(), 1, idx, sc)
+    idx = idx.cpu().numpy()[:, 0]
+    sc = sc.cpu().numpy()[:, 0]
+    assert idx[5] == 37 and idx[200] == 299
+    S64 = np.stack([oracle.scores(A, R[b]) for b in range(B)])
+    top2 = np.sort(S64, axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) > 1e-5 * top2[:, 1]
+    assert np.array_equal(idx[clear], np.argmax(S64, axis=1)[clear])
+    np.testing.assert_allclose(sc, S64[np.arange(B), idx], rtol=1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_1024x8192_sampled(prec):
+    """The 1024 x 8192, B = 4096, S = 32 workload at full size in the launch configuration the
+    benchmark times (graph replay); 48 sampled signals are checked against the oracle."""
+    w = gen.get_config("gaussian_1024x8192_s32_b4096")
+    A = gen.dictionary(w)
+    Y, *_ = gen.signals(w, A)
+    r = solve(prec, A, Y, w.S)
+    rows = np.linspace(0, w.B - 1, 48).astype(int)
+    ref = oracle.omp_batch(A, Y[rows], w.S)
+    st = parity.compare(A, Y[rows], ref, r["sup"][rows], r["X"][rows], r["n_iter"][rows],
+                        r["resid"][rows], rows=rows)
+    assert st["tie_diverged"] <= 2, st
+    assert np.all(r["n_iter"] == w.S)

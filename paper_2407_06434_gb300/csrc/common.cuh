@@ -2,7 +2,7 @@
 //
 // Data layout in HBM (one handle):
 //   dictionary (prepared once per A):
-//     A32   N x Mp  float   atom rows, zero padded to Mp (multiple of 64)   -- update / rescoring
+//     A32   N x Mp  float   atom rows, zero padded to Mp (64; 128 for E4M3) -- update / rescoring
 //     A16   N x Mp  bf16    RN-even copy                                     -- BF16 correlation
 //     A8    N x Mp  e4m3    per-atom scaled copy, sa[n] = amax_n / 448        -- FP8 correlation
 //     inv_norm[N] float = 1/||a_n|| (from FP64), norm2[N] double = ||a_n||^2
@@ -32,17 +32,21 @@
 
 namespace ompk {
 
-constexpr int kMpAlign = 64;          // M padding: one 128-byte row of a BF16 K-chunk
+constexpr int kMpAlign = 64;          // M padding (x2 for E4M3): one 128-byte K stage
 constexpr int kSigTile = 128;         // signals per correlation tile (TMEM lanes)
 constexpr int kMaxTopk = 8;
+constexpr int kPieces = 32;           // candidate slots per position (quantised paths)
 constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a||^2
 constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
 
 struct Ws {
   int M, Mp, N, Smax, Bmax, Bpad;
   int prec;        // omp_precision
-  int topk;        // candidates kept per signal by the correlation (1 for FP32)
-  int pieces;      // candidate pieces per position (quantised paths)
+  int topk;        // candidates rescored per signal (1 for FP32)
+  int pieces;      // candidate slots per position (quantised paths)
+  int tc_grid;     // tensor-core correlation: persistent grid size
+  int tc_tn;       // atom tiles of 256
+  int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
   int64_t Fstride; // Smax (Smax + 1) / 2
   // dictionary
   float* A32;
@@ -50,6 +54,7 @@ struct Ws {
   uint8_t* A8;
   float* sa;
   float* inv_norm;
+  float* escale;   // quantised paths: score scale per atom (1/||a|| or s_a/||a||), padded
   double* norm2;
   float* gram;
   // signal state
@@ -136,6 +141,31 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return out;
 }
 
+// Persistent schedule of the tensor-core correlation (shared by the correlation kernel, which
+// writes candidate slots, and the kernels that merge them). Units u = s * Tn + t over signal
+// tiles s and atom tiles t; Geff CTAs each own a contiguous range of at least `cmin` units.
+__host__ __device__ __forceinline__ void tc_sched(int L, int G, int Tn, int cmin, int& T, int& Geff) {
+  const int St = (L + kSigTile - 1) / kSigTile;
+  T = St * Tn;
+  int g = T / cmin;
+  if (g < 1) g = 1;
+  Geff = g < G ? g : G;
+}
+__host__ __device__ __forceinline__ int tc_start(int g, int T, int Geff) {
+  return static_cast<int>(static_cast<long long>(g) * T / Geff);
+}
+// the CTA whose range contains unit u
+__host__ __device__ __forceinline__ int tc_owner(int u, int T, int Geff) {
+  return static_cast<int>((static_cast<long long>(u + 1) * Geff - 1) / T);
+}
+// candidate slots [0, count) of live position p hold its signal tile's pieces
+__device__ __forceinline__ int tc_piece_count(const Ws& ws, int L, int p) {
+  int T, Geff;
+  tc_sched(L, ws.tc_grid, ws.tc_tn, ws.tc_cmin, T, Geff);
+  const int s = p / kSigTile;
+  return tc_owner(s * ws.tc_tn + ws.tc_tn - 1, T, Geff) - tc_owner(s * ws.tc_tn, T, Geff) + 1;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 void launch_prep(const Ws& ws, const float* A, cudaStream_t s);
@@ -153,7 +183,8 @@ cudaError_t configure_update_kernels(const Ws& ws);
 
 // tensor-core correlation (corr_tc.cu)
 struct TcPlan;
-int tc_pieces(int Mp, int N, int Bpad, int sm_count);
+int tc_pieces();
+void tc_fill_sched(Ws& ws, int sm_count);
 cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan);
 void tc_destroy(TcPlan* plan);
 void launch_corr_tc(const Ws& ws, const TcPlan* plan, int k, int B, cudaStream_t s);

@@ -28,6 +28,10 @@ __global__ void __launch_bounds__(256) prep_kernel(Ws ws, const float* __restric
       ws.norm2[n] = s;
       ws.inv_norm[n] = s > 0.0 ? static_cast<float>(1.0 / sqrt(s)) : 0.f;
     }
+    if (lane == 0 && ws.escale) {
+      const float in = s > 0.0 ? static_cast<float>(1.0 / sqrt(s)) : 0.f;
+      ws.escale[n] = ws.prec == OMP_PREC_FP8_E4M3 ? (amax > 0.f ? amax / 448.f : 0.f) * in : in;
+    }
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat16* a16 = ws.A16 + static_cast<size_t>(n) * ws.Mp;
       for (int m = lane; m < ws.Mp; m += 32) a16[m] = __float2bfloat16_rn(a32[m]);

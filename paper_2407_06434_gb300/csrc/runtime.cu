@@ -247,7 +247,9 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   h->sm_count = prop.multiProcessorCount;
   Ws& ws = h->ws;
   ws.M = static_cast<int>(d.M);
-  ws.Mp = static_cast<int>((d.M + kMpAlign - 1) / kMpAlign * kMpAlign);
+  // one tensor-core K stage is 128 bytes: 64 BF16 or 128 E4M3 elements
+  const int64_t malign = d.precision == OMP_PREC_FP8_E4M3 ? 2 * kMpAlign : kMpAlign;
+  ws.Mp = static_cast<int>((d.M + malign - 1) / malign * malign);
   ws.N = static_cast<int>(d.N);
   ws.Smax = d.max_iters;
   ws.Bmax = static_cast<int>(d.max_batch);
@@ -255,13 +257,16 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ws.prec = d.precision;
   ws.topk = d.precision == OMP_PREC_FP32 ? 1 : h->d.rescore_topk;
   ws.Fstride = static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2;
-  ws.pieces = d.precision == OMP_PREC_FP32 ? 0 : tc_pieces(ws.Mp, ws.N, ws.Bpad, h->sm_count);
+  ws.pieces = d.precision == OMP_PREC_FP32 ? 0 : tc_pieces();
+  if (d.precision != OMP_PREC_FP32) tc_fill_sched(ws, h->sm_count);
   const size_t N = ws.N, Mp = ws.Mp, Bm = ws.Bmax, Bp = ws.Bpad, Sm = ws.Smax;
   const size_t qbytes = d.precision == OMP_PREC_BF16 ? 2 : 1;
   bool ok = true;
   ok = ok && dalloc(h, &ws.A32, N * Mp);
   if (d.precision == OMP_PREC_BF16) ok = ok && dalloc(h, &ws.A16, N * Mp);
   if (d.precision == OMP_PREC_FP8_E4M3) ok = ok && dalloc(h, &ws.A8, N * Mp) && dalloc(h, &ws.sa, N);
+  const size_t Npad = (N + 255) / 256 * 256;
+  if (d.precision != OMP_PREC_FP32) ok = ok && dalloc(h, &ws.escale, Npad);
   ok = ok && dalloc(h, &ws.inv_norm, N) && dalloc(h, &ws.norm2, N) && dalloc(h, &ws.gram, N * N);
   ok = ok && dalloc(h, &ws.R32, Bm * Mp);
   if (d.precision != OMP_PREC_FP32) {
@@ -288,6 +293,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
     return OMP_ERR_OUT_OF_MEMORY;
   }
   bool cuda_ok = cudaMemset(ws.err, 0, sizeof(unsigned)) == cudaSuccess &&
+                 (!ws.escale || cudaMemset(ws.escale, 0, Npad * sizeof(float)) == cudaSuccess) &&
                  cudaMemset(ws.cand1, 0, Bm * sizeof(unsigned long long)) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  configure_update_kernels(ws) == cudaSuccess;

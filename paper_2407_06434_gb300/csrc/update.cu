@@ -209,9 +209,9 @@ __global__ void __launch_bounds__(256) update_kernel(Ws ws, int k, int S, float 
     __shared__ int cidx_s[kMaxTopk];
     __shared__ float cval_s[kMaxTopk];
     if (warp == 0) {
-      const int total = ws.pieces * kMaxTopk;
-      const float* cs = ws.cand_s + static_cast<size_t>(p) * total;
-      const int* ci = ws.cand_i + static_cast<size_t>(p) * total;
+      const int total = tc_piece_count(ws, L, p) * kMaxTopk;
+      const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+      const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
       // each lane keeps its slice; extract the best 8 one at a time
       float vs[8];
       int vi[8];
@@ -461,9 +461,9 @@ __global__ void __launch_bounds__(32) topk_out_kernel(Ws ws, const CallArgs* arg
     }
     return;
   }
-  const int total = ws.pieces * kMaxTopk;
-  const float* cs = ws.cand_s + static_cast<size_t>(p) * total;
-  const int* ci = ws.cand_i + static_cast<size_t>(p) * total;
+  const int total = tc_piece_count(ws, ws.cnt[1], p) * kMaxTopk;
+  const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+  const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
   float vs[8];
   int vi[8];
 #pragma unroll

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "bf16", "fp8"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -214,3 +214,51 @@ def test_full_size_1024x8192_sampled(prec):
                         r["resid"][rows], rows=rows)
     assert st["tie_diverged"] <= 2, st
     assert np.all(r["n_iter"] == w.S)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_correlate_top8_quantised(prec):
+    """Tensor-core correlation: the top-8 atoms per signal equal a CPU top-8 of the scores
+    computed exactly (FP64) from the same quantised operands (BF16 round-to-nearest-even, or
+    E4M3 with per-atom and per-signal scales), wherever the CPU's 8th and 9th scores are apart
+    by more than 1e-4 relative; exact ties made by duplicated atoms resolve to the lower index.
+    N = 1000 gives a partial last atom tile, B = 300 a partial last signal tile."""
+    from oracle import quant
+    from paper_2407_06434_gb300 import omp
+    rng = np.random.default_rng(12)
+    M, N, B = 200, 1000, 300
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    A[:, 900] = A[:, 10]
+    A = np.asfortranarray(A)
+    R = rng.standard_normal((B, M)).astype(np.float32)
+    R[7] = 3.0 * A[:, 10]
+    s = omp.OmpSolver(M, N, max_batch=B, max_iters=1, precision=prec)
+    idx = torch.empty((B, 8), dtype=torch.int32, device="cuda")
+    sc = torch.empty((B, 8), dtype=torch.float32, device="cuda")
+    omp.omp_correlate_topk(s.h, dev_dict(A), torch.from_numpy(R).cuda(), 8, idx, sc)
+    idx = idx.cpu().numpy()
+    sc = sc.cpu().numpy()
+    s.close()
+    At = np.ascontiguousarray(A.T)
+    inv_norm = (1.0 / np.sqrt(np.sum(At.astype(np.float64) ** 2, axis=1))).astype(np.float32)
+    if prec == "bf16":
+        Aq = quant.bf16_round(At).astype(np.float64)
+        Rq = quant.bf16_round(R).astype(np.float64)
+        esc = inv_norm.astype(np.float64)
+    else:
+        ca, sa = quant.fp8_scale_rows(At)
+        cr, _ = quant.fp8_scale_rows(R)
+        Aq = quant.e4m3_value(ca)
+        Rq = quant.e4m3_value(cr)
+        esc = (sa * inv_norm).astype(np.float32).astype(np.float64)
+    S = np.abs(Rq @ Aq.T) * esc[None, :]
+    assert idx[7, 0] == 10 and 900 in idx[7]          # tie: 10 before 900
+    checked = 0
+    for b in range(B):
+        order = np.lexsort((np.arange(N), -S[b]))
+        s8, s9 = S[b, order[7]], S[b, order[8]]
+        if s8 - s9 > 1e-4 * s8:
+            assert set(idx[b]) == set(order[:8]), b
+            np.testing.assert_allclose(np.sort(sc[b])[::-1], S[b, order[:8]], rtol=2e-5)
+            checked += 1
+    assert checked > 0.9 * B

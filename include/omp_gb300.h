@@ -140,6 +140,32 @@ omp_status omp_profile_enable(omp_handle h, int32_t enable);
 omp_status omp_profile_read(omp_handle h, int32_t S, float* corr_ms_host, float* update_ms_host,
                             int32_t* live_host, void* stream);
 
+/* Largest B that omp_correlate_argmax_noalloc accepts. Its scratch is a fixed device array of
+ * this many 8-byte keys (512 KiB), which every GPU that loads this library keeps until the
+ * process exits. */
+#define OMP_NOALLOC_MAX_SIGNALS 65536
+
+/* Correlate-and-select that allocates nothing. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running under a fixed memory
+ * budget or inside a framework that owns every device allocation (cudaMalloc synchronises the
+ * device and can fail at run time) -- and for callers that need one scoring pass without
+ * creating a handle (omp_create allocates a whole solver's workspaces).
+ *   A          device, M x N column-major dictionary (any column norms; they are computed here)
+ *   R          device, B x M row-major residuals (or signals)
+ *   idx_out    device, B int32: argmax_n |<r_b, a_n>| / ||a_n||, lowest index on exact ties
+ *              (-1 if every atom has zero norm)
+ *   score_out  device, B float: that score
+ * The correlation runs in FP32 on the CUDA cores. Runs on the calling thread's current device;
+ * every pointer must be on it and 4-byte aligned. B > OMP_NOALLOC_MAX_SIGNALS (or any other bad
+ * argument) returns OMP_ERR_INVALID_ARGUMENT with nothing enqueued. The first call on a device
+ * looks up the scratch array's device address (a one-time set-up), so make that first call
+ * before any stream capture. All calls on a device share the one scratch array; each call
+ * clears what it uses first, but calls that overlap on the GPU (unordered streams) race and
+ * may return each other's results. */
+omp_status omp_correlate_argmax_noalloc(const float* A, const float* R, int64_t M, int64_t N,
+                                        int64_t B, int32_t* idx_out, float* score_out,
+                                        void* stream);
+
 /* Read and clear the device error word (OMP_DEVERR_* bits); synchronises the handle's work on
  * `stream` first. Returns OMP_ERR_DEVICE_TIMEOUT if the timeout bit was set, OMP_ERR_NUMERICAL
  * if only the non-finite bit was set, else OMP_OK. */

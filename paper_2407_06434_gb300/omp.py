@@ -29,7 +29,9 @@ STOP_ITERS, STOP_EPS, STOP_DEPENDENT, STOP_ZERO = 0, 1, 2, 3
 # every symbol include/omp_gb300.h declares
 EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_dictionary",
            "omp_solve_batch", "omp_solve_batch_ex", "omp_solve_batch_host", "omp_correlate_topk",
-           "omp_get_error", "omp_status_string", "omp_profile_enable", "omp_profile_read"]
+           "omp_get_error", "omp_status_string", "omp_profile_enable", "omp_profile_read",
+           "omp_correlate_argmax_noalloc"]
+NOALLOC_MAX_SIGNALS = 65536
 
 
 class omp_desc(ctypes.Structure):
@@ -73,6 +75,7 @@ def load(path: Optional[str] = None):
         "omp_status_string": (ctypes.c_char_p, [_I32]),
         "omp_profile_enable": (_I32, [_P, _I32]),
         "omp_profile_read": (_I32, [_P, _I32, _P, _P, _P, _P]),
+        "omp_correlate_argmax_noalloc": (_I32, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +216,19 @@ def omp_profile_read(h: Handle, S: int, stream=None):
     _check(load().omp_profile_read(h.ptr, S, corr.ctypes.data_as(_P), upd.ctypes.data_as(_P),
                                    live.ctypes.data_as(_P), _stream(stream)), "omp_profile_read")
     return corr, upd, live
+
+
+def omp_correlate_argmax_noalloc(A, R, idx_out, score_out, stream=None):
+    """Allocation-free argmax of |<r_b, a_n>| / ||a_n|| for callers that cannot allocate device
+    memory (see include/omp_gb300.h). A: (M, N) column-major; R: (B, M); idx_out: (B,) int32;
+    score_out: (B,) float32. Raises OmpError(OMP_ERR_INVALID_ARGUMENT) for
+    B > NOALLOC_MAX_SIGNALS."""
+    M, N = A.shape
+    if A.stride() != (1, M):
+        raise ValueError("A must be column-major (stride (1, M))")
+    _check(load().omp_correlate_argmax_noalloc(_ptr(A), _ptr(R), M, N, R.shape[0], _ptr(idx_out),
+                                               _ptr(score_out), _stream(stream)),
+           "omp_correlate_argmax_noalloc")
 
 
 def omp_status_string(status: int) -> str:

@@ -59,7 +59,7 @@ typedef enum {
 #define OMP_DEVERR_BAD_STATE 0x4     /* an internal index was out of range (skipped) */
 
 typedef struct omp_desc {
-  int64_t M;             /* signal length (rows of A), 1 <= M <= 16384 */
+  int64_t M;             /* signal length (rows of A), 1 <= M <= 8192 */
   int64_t N;             /* number of atoms (columns of A), 2 <= N <= 65536 */
   int64_t max_batch;     /* largest B any solve on this handle will pass, >= 1 */
   int32_t max_iters;     /* largest S any solve will pass, 1 <= max_iters <= min(M, N, 256) */

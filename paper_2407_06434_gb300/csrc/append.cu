@@ -1,0 +1,401 @@
+// Per-iteration selection, inverse-Cholesky append and residual update, one group of W warps
+// per live signal (W = 1 for padded lengths up to 1024, up to 8 for 8192).
+//
+// Iteration k (0-based; the paper's k+1), following Sec. 2.3:
+//   n*    the correlation's pick (FP32 path) or the best of its top-8 rescored in FP32
+//   w     = A_S^T a_{n*}          read from the Gram matrix row n* (Sec. 2.2 precompute)
+//   z     = F_k^T w               FP64
+//   delta = ||a_{n*}||^2 - ||z||^2; the atom is dependent if delta <= 1e-10 ||a_{n*}||^2
+//   gamma = 1 / sqrt(delta)       FP64: the diagonal of the new inverse-Cholesky column
+//   F[:,k] = [-gamma F_k z ; gamma]
+//   q     = A_{S+n*} F[:,k]       the new orthonormal direction (FP32 gather of k+1 atom rows)
+//   b_k   = q^T r,  r <- r - b_k q (y_hat = A_k F_k (A_k F_k)^T y built one term at a time)
+//
+// Layout of the work: the residual and q live in registers, sliced over the group's lanes in
+// float4 slots (slot s of a row belongs to lane s mod 32 of warp (s / 32) mod W). The small
+// triangular work runs in the group's first warp, lane-parallel over rows or columns of F.
+// GB300 issues FP64 at a small fraction of its FP32 rate, so only the Schur complement, gamma
+// and the stored factor are FP64; z and F z use an FP32 copy of F. Group members meet only at
+// group-scoped named barriers.
+#include "common.cuh"
+
+namespace ompk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlk = 8;  // z blocks of 32 columns: Smax <= 256 (NB <= kMaxBlk per kernel)
+
+__device__ __forceinline__ void group_sync(int W, int grp) {
+  if (W == 1)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(W * 32) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct GroupSmem {
+  float* w;      // Smax: A_S^T a_{n*} (Gram row entries)
+  float* z;      // Smax: F^T w
+  float* f;      // Smax + 1: new F column (FP32 copy used by the gather)
+  int* sup;      // Smax + 1: support including n*
+  float* cpart;  // 8 x 8: rescoring partial dot products [candidate][warp]
+  int* cidx;     // 8
+  double* part;  // 16: per-warp partials of b and ||r||^2
+  int* scal;     // 4: n*, dependent flag
+};
+
+__host__ __device__ __forceinline__ size_t group_bytes(int Smax) {
+  const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
+                   8 * 4 + 16 * 8 + 16;
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, int Smax) {
+  unsigned char* g = base + grp * group_bytes(Smax);
+  GroupSmem s;
+  s.part = reinterpret_cast<double*>(g);
+  s.f = reinterpret_cast<float*>(g + 16 * 8);
+  s.sup = reinterpret_cast<int*>(s.f + Smax + 1);
+  s.cpart = reinterpret_cast<float*>(s.sup + Smax + 1);
+  s.cidx = reinterpret_cast<int*>(s.cpart + 64);
+  s.scal = s.cidx + 8;
+  s.w = reinterpret_cast<float*>(s.scal + 4);
+  s.z = s.w + Smax;
+  return s;
+}
+
+template <int W, int V, int NB>
+__global__ void __launch_bounds__(kThreads, 2)
+    append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
+  const bool top1 = ws.prec == OMP_PREC_FP32;
+  constexpr int GPB = 8 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp / W, wig = warp - grp * W;
+  const int L = ws.cnt[k + 1];
+  const int p = blockIdx.x * GPB + grp;
+  if (p >= L) return;  // the whole group leaves together
+  const int id = ws.live[k & 1][p];
+  extern __shared__ __align__(16) unsigned char smem[];
+  GroupSmem gs = group_smem(smem, grp, ws.Smax);
+
+  const int M4 = ws.Mp >> 2;
+  const float4* rrow = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
+  float4 r[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int s = t * (W * 32) + wig * 32 + lane;
+    r[t] = s < M4 ? rrow[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  // ---------------------------------------------------------------- selection
+  int ns;
+  if (top1) {
+    ns = key_index(ws.cand1[p]);
+  } else {
+    if (wig == 0) {
+      const int total = tc_piece_count(ws, L, p) * kMaxTopk;
+      const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+      const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+      float vs[8];
+      int vi[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int e = lane + 32 * t;
+        const bool ok = e < total;
+        vs[t] = ok ? cs[e] : -1.f;
+        vi[t] = ok ? ci[e] : 0x7fffffff;
+        if (vi[t] < 0) {
+          vs[t] = -1.f;
+          vi[t] = 0x7fffffff;
+        }
+      }
+      for (int sel = 0; sel < ws.topk; ++sel) {
+        float bs = -2.f;
+        int bi = 0x7fffffff, bt = -1;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (better(vs[t], vi[t], bs, bi)) {
+            bs = vs[t];
+            bi = vi[t];
+            bt = t;
+          }
+        float g_s = bs;
+        int g_i = bi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float os = __shfl_xor_sync(0xffffffffu, g_s, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, g_i, o);
+          if (better(os, oi, g_s, g_i)) {
+            g_s = os;
+            g_i = oi;
+          }
+        }
+        if (bt >= 0 && bi == g_i && bs == g_s) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (t == bt) {
+              vs[t] = -2.f;
+              vi[t] = 0x7fffffff;
+            }
+        }
+        if (lane == 0) gs.cidx[sel] = (g_i >= 0 && g_i < ws.N) ? g_i : -1;
+      }
+    }
+    group_sync(W, grp);
+    // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row
+    for (int c = 0; c < ws.topk; ++c) {
+      const int n = gs.cidx[c];
+      float acc = 0.f;
+      if (n >= 0) {
+        const float4* a4 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n) * ws.Mp);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          const int s = t * (W * 32) + wig * 32 + lane;
+          if (s < M4) {
+            const float4 a = __ldg(a4 + s);
+            acc += a.x * r[t].x + a.y * r[t].y + a.z * r[t].z + a.w * r[t].w;
+          }
+        }
+      }
+      acc = warp_sum_f(acc);
+      if (lane == 0) gs.cpart[c * 8 + wig] = acc;
+    }
+    group_sync(W, grp);
+    if (wig == 0) {
+      float sc = -2.f;
+      int ix = 0x7fffffff;
+      if (lane < ws.topk && gs.cidx[lane] >= 0) {
+        float v = 0.f;
+        for (int w = 0; w < W; ++w) v += gs.cpart[lane * 8 + w];
+        ix = gs.cidx[lane];
+        sc = fabsf(v) * __ldg(ws.inv_norm + ix);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, sc, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (better(os, oi, sc, ix)) {
+          sc = os;
+          ix = oi;
+        }
+      }
+      if (lane == 0) gs.scal[0] = ix;
+    }
+    group_sync(W, grp);
+    ns = gs.scal[0];
+  }
+  if (ns < 0 || ns >= ws.N) {
+    if (wig == 0 && lane == 0) {
+      atomicOr(ws.err, OMP_DEVERR_BAD_STATE);
+      ws.flag[p] = 0;
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- append (first warp)
+  // z and F z run in FP32 on the FP32 copy of F: their input w comes from the FP32 Gram matrix,
+  // so FP64 arithmetic there would add no accuracy. The Schur complement delta, gamma and the
+  // stored factor (used by the back-substitution) are FP64.
+  double* Fg = ws.F + static_cast<size_t>(id) * ws.Fstride;
+  float* Ff = ws.F32 + static_cast<size_t>(id) * ws.Fstride;
+  if (wig == 0) {
+    const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
+    const float* grow = ws.gram + static_cast<size_t>(ns) * ws.N;
+    for (int i = lane; i < k; i += 32) {
+      const int si = supg[i];
+      gs.sup[i] = si;
+      gs.w[i] = __ldg(grow + si);
+    }
+    __syncwarp();
+    // z_j = sum_{i<=j} F[i,j] w_i, lane slot j = lane + 32 t
+    float zl[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) zl[t] = 0.f;
+    for (int i = 0; i < k; ++i) {
+      const float wi = gs.w[i];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int j = lane + 32 * t;
+        if (j < k && i <= j) zl[t] = fmaf(Ff[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
+      }
+    }
+    double zz = 0.0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) {
+        gs.z[j] = zl[t];
+        zz += static_cast<double>(zl[t]) * static_cast<double>(zl[t]);
+      }
+    }
+    zz = warp_sum(zz);
+    const double nrm2 = ws.norm2[ns];
+    const double delta = nrm2 - zz;
+    const bool dep = !(delta > kDepRtol * nrm2);
+    if (lane == 0) gs.scal[1] = dep ? 1 : 0;
+    __syncwarp();
+    if (!dep) {
+      const double gamma = 1.0 / sqrt(delta);
+      // u_i = sum_{j>=i} F[i,j] z_j, lane slot i; one coalesced column per j
+      float ul[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) ul[t] = 0.f;
+      for (int j = 0; j < k; ++j) {
+        const float zj = gs.z[j];
+        const float* col = Ff + static_cast<size_t>(j) * (j + 1) / 2;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          const int i = lane + 32 * t;
+          if (i <= j) ul[t] = fmaf(col[i], zj, ul[t]);
+        }
+      }
+      const size_t off = static_cast<size_t>(k) * (k + 1) / 2;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int i = lane + 32 * t;
+        if (i < k) {
+          const double fv = -gamma * static_cast<double>(ul[t]);
+          const float f32 = static_cast<float>(fv);
+          Fg[off + i] = fv;
+          Ff[off + i] = f32;
+          gs.f[i] = f32;
+        }
+      }
+      if (lane == 0) {
+        Fg[off + k] = gamma;
+        Ff[off + k] = static_cast<float>(gamma);
+        gs.f[k] = static_cast<float>(gamma);
+        gs.sup[k] = ns;
+      }
+    }
+  }
+  group_sync(W, grp);
+  if (gs.scal[1]) {
+    if (wig == 0 && lane == 0) {
+      ws.flag[p] = 0;
+      ws.stop[id] = kStopDependent;
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- q, b, residual update
+  float4 q[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) q[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int na = k + 1;
+  int a = 0;
+  for (; a + 2 <= na; a += 2) {
+    const float f0 = gs.f[a], f1 = gs.f[a + 1];
+    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
+    const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 1]) * ws.Mp);
+    float4 v0[V], v1[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = t * (W * 32) + wig * 32 + lane;
+      v0[t] = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v1[t] = s < M4 ? __ldg(a1 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      q[t].x = fmaf(f1, v1[t].x, fmaf(f0, v0[t].x, q[t].x));
+      q[t].y = fmaf(f1, v1[t].y, fmaf(f0, v0[t].y, q[t].y));
+      q[t].z = fmaf(f1, v1[t].z, fmaf(f0, v0[t].z, q[t].z));
+      q[t].w = fmaf(f1, v1[t].w, fmaf(f0, v0[t].w, q[t].w));
+    }
+  }
+  if (a < na) {
+    const float f0 = gs.f[a];
+    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = t * (W * 32) + wig * 32 + lane;
+      const float4 v = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      q[t].x = fmaf(f0, v.x, q[t].x);
+      q[t].y = fmaf(f0, v.y, q[t].y);
+      q[t].z = fmaf(f0, v.z, q[t].z);
+      q[t].w = fmaf(f0, v.w, q[t].w);
+    }
+  }
+  float bp = 0.f;
+#pragma unroll
+  for (int t = 0; t < V; ++t) bp += q[t].x * r[t].x + q[t].y * r[t].y + q[t].z * r[t].z + q[t].w * r[t].w;
+  bp = warp_sum_f(bp);
+  if (lane == 0) gs.part[wig] = bp;
+  group_sync(W, grp);
+  double b = 0.0;
+  for (int w = 0; w < W; ++w) b += gs.part[w];  // W <= 8 partials
+  const float bf = static_cast<float>(b);
+  float4* rw = reinterpret_cast<float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
+  float rr = 0.f;
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int s = t * (W * 32) + wig * 32 + lane;
+    r[t].x = fmaf(-bf, q[t].x, r[t].x);
+    r[t].y = fmaf(-bf, q[t].y, r[t].y);
+    r[t].z = fmaf(-bf, q[t].z, r[t].z);
+    r[t].w = fmaf(-bf, q[t].w, r[t].w);
+    if (s < M4) rw[s] = r[t];
+    rr += r[t].x * r[t].x + r[t].y * r[t].y + r[t].z * r[t].z + r[t].w * r[t].w;
+  }
+  rr = warp_sum_f(rr);
+  if (lane == 0) gs.part[8 + wig] = rr;
+  group_sync(W, grp);
+  if (wig == 0 && lane == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
+    const double rn = sqrt(tot);
+    ws.bv[static_cast<size_t>(id) * ws.Smax + k] = b;
+    ws.sup[static_cast<size_t>(id) * ws.Smax + k] = ns;
+    ws.niter[id] = k + 1;
+    ws.rnorm[id] = static_cast<float>(rn);
+    const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ws.ynorm[id])
+                               : static_cast<double>(eps);
+    int cont = 1;
+    if (rn <= thr) {
+      cont = 0;
+      ws.stop[id] = kStopEps;
+    } else if (k + 1 >= S) {
+      cont = 0;
+      ws.stop[id] = kStopIters;
+    }
+    ws.flag[p] = static_cast<uint8_t>(cont);
+  }
+}
+
+// W warps per signal and V float4 slots per lane cover Mp <= 128 W V; NB blocks of 32 columns
+// cover Smax <= 32 NB.
+template <int W, int V, int NB>
+void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  constexpr int GPB = 8 / W;
+  const size_t smem = group_bytes(ws.Smax) * GPB;
+  append_update_kernel<W, V, NB><<<(B + GPB - 1) / GPB, kThreads, smem, s>>>(ws, k, S, eps, eps_rel);
+}
+
+template <int NB>
+void launch_nb(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  if (ws.Mp <= 256) launch_t<1, 2, NB>(ws, k, B, S, eps, eps_rel, s);
+  else if (ws.Mp <= 1024) launch_t<1, 8, NB>(ws, k, B, S, eps, eps_rel, s);
+  else if (ws.Mp <= 2048) launch_t<2, 8, NB>(ws, k, B, S, eps, eps_rel, s);
+  else if (ws.Mp <= 4096) launch_t<4, 8, NB>(ws, k, B, S, eps, eps_rel, s);
+  else launch_t<8, 8, NB>(ws, k, B, S, eps, eps_rel, s);
+}
+
+}  // namespace
+
+cudaError_t configure_update_kernels(const Ws& ws) {
+  if (ws.Mp > 8192 || ws.Smax > 32 * kMaxBlk) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  if (ws.Smax <= 32) launch_nb<1>(ws, k, B, S, eps, eps_rel, s);
+  else if (ws.Smax <= 128) launch_nb<4>(ws, k, B, S, eps, eps_rel, s);
+  else launch_nb<8>(ws, k, B, S, eps, eps_rel, s);
+}
+
+}  // namespace ompk

@@ -68,6 +68,7 @@ struct Ws {
   float* cand_s;
   int* cand_i;
   double* F;
+  float* F32;      // FP32 copy of F (same packing) for the per-iteration triangular products
   double* bv;
   int* sup;
   float* ynorm;
@@ -178,7 +179,6 @@ void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cu
 void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStream_t s);
 void launch_topk_out(const Ws& ws, const CallArgs* args, int B, int topk, cudaStream_t s);
 void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s);
-size_t update_smem_bytes(const Ws& ws);
 cudaError_t configure_update_kernels(const Ws& ws);
 
 // tensor-core correlation (corr_tc.cu)

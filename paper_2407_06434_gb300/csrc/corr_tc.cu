@@ -40,7 +40,9 @@ constexpr int B_BYTES = BN * KB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 2 * BN;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int STAGE_ROW = 36;  // floats per staged score row (float4 stores without conflicts)
+constexpr int EPI_STAGE_BYTES = 4 * 32 * STAGE_ROW * 4;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + EPI_STAGE_BYTES;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -140,7 +142,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
       "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
@@ -151,6 +153,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
         "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -304,6 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------------------------ epilogue
     const int lg = warp & 3;                 // TMEM lane quarter this warp may access
     const int row = lg * 32 + lane;          // signal row within the tile
+    float* stage_row = reinterpret_cast<float*>(bars_gen + 256) + ((warp - 2) * 32 + lane) * STAGE_ROW;
     int acc = 0;
     uint32_t aph = 0;
     int cur_s = -1;
@@ -345,25 +350,45 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) + static_cast<uint32_t>(acc * BN);
       const int n0 = t * BN;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(taddr + c0, v);
-        const int nb = n0 + c0;
+      // Scores of a 32-column chunk go to this lane's row of the warp's staging buffer; a
+      // compare-only pass marks the columns above the current 8th score, and only those are
+      // inserted (few per chunk once the list is warm), so the warp does not diverge per column.
+      // The next chunk's TMEM load is in flight while this one is scored.
+      uint32_t va[32], vb[32];
+      tmem_ld32_issue(taddr, va);
+      tmem_ld_wait();
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t (&cur)[32] = (c & 1) ? vb : va;
+        uint32_t (&nxt)[32] = (c & 1) ? va : vb;
+        if (c + 1 < BN / 32) tmem_ld32_issue(taddr + (c + 1) * 32, nxt);
+        const int nb = n0 + c * 32;
         const int lim = min(32, ws.N - nb);
         const float4* sc4 = reinterpret_cast<const float4*>(ws.escale + nb);
+        const float thr = ts[7];
+        uint32_t mask = 0;
 #pragma unroll
         for (int j4 = 0; j4 < 8; ++j4) {
           const float4 sc = __ldg(sc4 + j4);
-          const float scl[4] = {sc.x, sc.y, sc.z, sc.w};
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = j4 * 4 + jj;
-            if (j < lim) {
-              const float score = fabsf(__uint_as_float(v[j])) * scl[jj];
-              if (score > ts[7]) top8_insert(ts, ti, score, nb + j);
-            }
-          }
+          float4 o;
+          o.x = fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x;
+          o.y = fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y;
+          o.z = fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z;
+          o.w = fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w;
+          mask |= (o.x > thr ? 1u : 0u) << (4 * j4 + 0);
+          mask |= (o.y > thr ? 1u : 0u) << (4 * j4 + 1);
+          mask |= (o.z > thr ? 1u : 0u) << (4 * j4 + 2);
+          mask |= (o.w > thr ? 1u : 0u) << (4 * j4 + 3);
+          *reinterpret_cast<float4*>(stage_row + 4 * j4) = o;
         }
+        if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
+        while (mask) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const float score = stage_row[j];
+          if (score > ts[7]) top8_insert(ts, ti, score, nb + j);
+        }
+        if (c + 1 < BN / 32) tmem_ld_wait();
       }
       tc_fence_before();
       __syncwarp();

@@ -224,7 +224,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   if (!desc || !out) return OMP_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   const omp_desc d = *desc;
-  if (d.M < 1 || d.M > 16384 || d.N < 2 || d.N > 65536 || d.max_batch < 1 ||
+  if (d.M < 1 || d.M > 8192 || d.N < 2 || d.N > 65536 || d.max_batch < 1 ||
       d.max_batch > (1 << 24) || d.max_iters < 1 || d.max_iters > 256 || d.max_iters > d.M ||
       d.max_iters > d.N || d.precision < 0 || d.precision > 2 || d.rescore_topk < 0 ||
       d.rescore_topk > kMaxTopk)
@@ -281,7 +281,8 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   }
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
-  ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
+  ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
+       dalloc(h, &ws.F32, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
        dalloc(h, &ws.sup, Bm * Sm);
   ok = ok && dalloc(h, &ws.ynorm, Bm) && dalloc(h, &ws.rnorm, Bm) && dalloc(h, &ws.niter, Bm) &&
        dalloc(h, &ws.stop, Bm) && dalloc(h, &ws.err, 1) && dalloc(h, &h->args_dev, 1);

@@ -1,16 +1,6 @@
-// Per-signal kernels of the OMP iteration: initialisation, live-set compaction, the
-// inverse-Cholesky append + residual update (one block per live signal), and the final
-// back-substitution.
-//
-// Update of one signal at iteration k (0-based; the paper's k+1), following Sec. 2.3:
-//   w   = A_S^T a_{n*}           read from the Gram matrix row n* (Sec. 2.2 precompute)
-//   z   = F_{k}^T w              (FP64)
-//   delta = ||a_{n*}||^2 - ||z||^2, dependent atom if delta <= 1e-10 ||a_{n*}||^2
-//   gamma = 1 / sqrt(delta)      (FP64; the diagonal of the new inverse-Cholesky column)
-//   F[:, k] = [-gamma F_k z ; gamma]
-//   q   = A_{S+n*} F[:, k]       the new orthonormal direction (FP32 gather of k+1 atom rows)
-//   b_k = q^T r,  r <- r - b_k q (so y_hat = A_k F_k (A_k F_k)^T y is built one term at a time)
-// and the coefficients come out at the end as x = F b (finalize, FP64).
+// Per-signal kernels around the OMP iteration: initialisation, live-set compaction, the final
+// back-substitution x = F b (FP64), and the top-k output of omp_correlate_topk. The per-iteration
+// append and residual update is in append.cu.
 #include "common.cuh"
 
 namespace ompk {
@@ -167,245 +157,6 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j) {
 
 void launch_compact(const Ws& ws, int j, int B, cudaStream_t s) {
   compact_kernel<<<(B + kCompactChunk - 1) / kCompactChunk, 256, 0, s>>>(ws, j);
-}
-
-// ------------------------------------------------------------------------------------ update
-size_t update_smem_bytes(const Ws& ws) {
-  // r (Mp) + q (Mp) floats | w, z (Smax) doubles | red (16) doubles | f (Smax+1) floats |
-  // support (Smax+1) ints
-  return static_cast<size_t>(2 * ws.Mp) * 4 + static_cast<size_t>(2 * ws.Smax + 16) * 8 +
-         static_cast<size_t>(ws.Smax + 1) * 8;
-}
-
-template <int TOPK>
-__global__ void __launch_bounds__(256) update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
-  const int L = ws.cnt[k + 1];
-  const int p = blockIdx.x;
-  if (p >= L) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int id = ws.live[k & 1][p];
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* r_s = reinterpret_cast<float*>(smem);
-  float* q_s = r_s + ws.Mp;
-  double* w_s = reinterpret_cast<double*>(q_s + ws.Mp);
-  double* z_s = w_s + ws.Smax;
-  double* red = z_s + ws.Smax;
-  float* f_s = reinterpret_cast<float*>(red + 16);
-  int* sup_s = reinterpret_cast<int*>(f_s + ws.Smax + 1);
-  __shared__ int nstar_s;
-
-  const int M4 = ws.Mp >> 2;
-  const float4* rg = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
-  for (int i = tid; i < M4; i += 256) reinterpret_cast<float4*>(r_s)[i] = rg[i];
-  const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
-  for (int i = tid; i < k; i += 256) sup_s[i] = supg[i];
-  __syncthreads();
-
-  // ---- selection: n* from the correlation's candidates
-  if (TOPK == 1) {
-    if (tid == 0) nstar_s = key_index(ws.cand1[p]);
-  } else {
-    // merge the pieces' top-8 lists (warp 0), then rescore the best `topk` in FP32
-    __shared__ int cidx_s[kMaxTopk];
-    __shared__ float cval_s[kMaxTopk];
-    if (warp == 0) {
-      const int total = tc_piece_count(ws, L, p) * kMaxTopk;
-      const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
-      const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
-      // each lane keeps its slice; extract the best 8 one at a time
-      float vs[8];
-      int vi[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int e = lane + 32 * t;
-        const bool ok = e < total;
-        vs[t] = ok ? cs[e] : -1.f;
-        vi[t] = ok ? ci[e] : 0x7fffffff;
-        if (vi[t] < 0) { vs[t] = -1.f; vi[t] = 0x7fffffff; }
-      }
-      for (int sel = 0; sel < ws.topk; ++sel) {
-        float bs = -2.f;
-        int bi = 0x7fffffff, bt = -1;
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-          if (better(vs[t], vi[t], bs, bi)) { bs = vs[t]; bi = vi[t]; bt = t; }
-        float gs = bs;
-        int gi = bi;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float os = __shfl_xor_sync(0xffffffffu, gs, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, gi, o);
-          if (better(os, oi, gs, gi)) { gs = os; gi = oi; }
-        }
-        if (bt >= 0 && bi == gi && bs == gs) {
-#pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (t == bt) { vs[t] = -2.f; vi[t] = 0x7fffffff; }
-        }
-        if (lane == 0) cidx_s[sel] = (gi >= 0 && gi < ws.N) ? gi : -1;
-      }
-    }
-    __syncthreads();
-    // warp w rescores candidate w: c = a^T r in FP32 from the FP32 atom row and FP32 residual
-    if (warp < ws.topk) {
-      const int n = cidx_s[warp];
-      float v = -1.f;
-      if (n >= 0) {
-        const float4* a4 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n) * ws.Mp);
-        double s = 0.0;
-        for (int i = lane; i < M4; i += 32) {
-          const float4 a = __ldg(a4 + i);
-          const float4 r = reinterpret_cast<const float4*>(r_s)[i];
-          s += static_cast<double>(a.x * r.x + a.y * r.y + a.z * r.z + a.w * r.w);
-        }
-        s = warp_sum(s);
-        v = fabsf(static_cast<float>(s)) * __ldg(ws.inv_norm + n);
-      }
-      if (lane == 0) cval_s[warp] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float bs = -2.f;
-      int bi = 0x7fffffff;
-      for (int c = 0; c < ws.topk; ++c)
-        if (cidx_s[c] >= 0 && better(cval_s[c], cidx_s[c], bs, bi)) { bs = cval_s[c]; bi = cidx_s[c]; }
-      nstar_s = bi;
-    }
-  }
-  __syncthreads();
-  const int ns = nstar_s;
-  if (ns < 0 || ns >= ws.N) {
-    if (tid == 0) {
-      atomicOr(ws.err, OMP_DEVERR_BAD_STATE);
-      ws.flag[p] = 0;
-    }
-    return;
-  }
-
-  // ---- w = A_S^T a_{n*} from the Gram row of n*
-  const float* grow = ws.gram + static_cast<size_t>(ns) * ws.N;
-  for (int i = tid; i < k; i += 256) w_s[i] = static_cast<double>(__ldg(grow + sup_s[i]));
-  __syncthreads();
-  // ---- z = F^T w: one warp per column j, z_j = sum_{i<=j} F[i,j] w_i
-  double* Fg = ws.F + static_cast<size_t>(id) * ws.Fstride;
-  for (int j = warp; j < k; j += 8) {
-    const double* col = Fg + static_cast<size_t>(j) * (j + 1) / 2;
-    double s = 0.0;
-    for (int i = lane; i <= j; i += 32) s += col[i] * w_s[i];
-    s = warp_sum(s);
-    if (lane == 0) z_s[j] = s;
-  }
-  __syncthreads();
-  double zz = 0.0;
-  for (int i = tid; i < k; i += 256) zz += z_s[i] * z_s[i];
-  zz = block_sum256(zz, red);
-  const double nrm2 = ws.norm2[ns];
-  const double delta = nrm2 - zz;
-  if (!(delta > kDepRtol * nrm2)) {
-    if (tid == 0) {
-      ws.flag[p] = 0;
-      ws.stop[id] = kStopDependent;
-    }
-    return;
-  }
-  const double gamma = 1.0 / sqrt(delta);
-  // ---- new column F[:, k] = [-gamma F z ; gamma]; thread i: u_i = sum_{j>=i} F[i,j] z_j
-  double* Fk = Fg + static_cast<size_t>(k) * (k + 1) / 2;
-  for (int i = tid; i < k; i += 256) {
-    double u = 0.0;
-    for (int j = i; j < k; ++j) u += Fg[static_cast<size_t>(j) * (j + 1) / 2 + i] * z_s[j];
-    const double f = -gamma * u;
-    Fk[i] = f;
-    f_s[i] = static_cast<float>(f);
-  }
-  if (tid == 0) {
-    Fk[k] = gamma;
-    f_s[k] = static_cast<float>(gamma);
-    sup_s[k] = ns;
-  }
-  __syncthreads();
-
-  // ---- q = A_{S+n*} F[:, k] (k+1 atom rows, float4 loads), b = q^T r
-  const int na = k + 1;
-  double bpart = 0.0;
-  for (int i = tid; i < M4; i += 256) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int a = 0;
-    for (; a + 4 <= na; a += 4) {
-      float4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        v[u] = __ldg(reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(sup_s[a + u]) * ws.Mp) + i);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float f = f_s[a + u];
-        acc.x = fmaf(f, v[u].x, acc.x);
-        acc.y = fmaf(f, v[u].y, acc.y);
-        acc.z = fmaf(f, v[u].z, acc.z);
-        acc.w = fmaf(f, v[u].w, acc.w);
-      }
-    }
-    for (; a < na; ++a) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(sup_s[a]) * ws.Mp) + i);
-      const float f = f_s[a];
-      acc.x = fmaf(f, v.x, acc.x);
-      acc.y = fmaf(f, v.y, acc.y);
-      acc.z = fmaf(f, v.z, acc.z);
-      acc.w = fmaf(f, v.w, acc.w);
-    }
-    reinterpret_cast<float4*>(q_s)[i] = acc;
-    const float4 r = reinterpret_cast<const float4*>(r_s)[i];
-    bpart += static_cast<double>(acc.x * r.x + acc.y * r.y + acc.z * r.z + acc.w * r.w);
-  }
-  const double b = block_sum256(bpart, red);
-  const float bf = static_cast<float>(b);
-  // ---- r <- r - b q, ||r||^2
-  float4* rw = reinterpret_cast<float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
-  double rr = 0.0;
-  for (int i = tid; i < M4; i += 256) {
-    float4 r = reinterpret_cast<const float4*>(r_s)[i];
-    const float4 q = reinterpret_cast<const float4*>(q_s)[i];
-    r.x = fmaf(-bf, q.x, r.x);
-    r.y = fmaf(-bf, q.y, r.y);
-    r.z = fmaf(-bf, q.z, r.z);
-    r.w = fmaf(-bf, q.w, r.w);
-    rw[i] = r;
-    rr += static_cast<double>(r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w);
-  }
-  rr = block_sum256(rr, red);
-  if (tid == 0) {
-    const double rn = sqrt(rr);
-    ws.bv[static_cast<size_t>(id) * ws.Smax + k] = b;
-    ws.sup[static_cast<size_t>(id) * ws.Smax + k] = ns;
-    ws.niter[id] = k + 1;
-    ws.rnorm[id] = static_cast<float>(rn);
-    const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ws.ynorm[id])
-                               : static_cast<double>(eps);
-    int cont = 1;
-    if (rn <= thr) {
-      cont = 0;
-      ws.stop[id] = kStopEps;
-    } else if (k + 1 >= S) {
-      cont = 0;
-      ws.stop[id] = kStopIters;
-    }
-    ws.flag[p] = static_cast<uint8_t>(cont);
-  }
-}
-
-cudaError_t configure_update_kernels(const Ws& ws) {
-  const int bytes = static_cast<int>(update_smem_bytes(ws));
-  cudaError_t e = cudaFuncSetAttribute(update_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(update_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  const size_t smem = update_smem_bytes(ws);
-  if (ws.topk == 1 && ws.prec == OMP_PREC_FP32)
-    update_kernel<1><<<B, 256, smem, s>>>(ws, k, S, eps, eps_rel);
-  else
-    update_kernel<8><<<B, 256, smem, s>>>(ws, k, S, eps, eps_rel);
 }
 
 // ---------------------------------------------------------------------------------- finalize

@@ -309,6 +309,84 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Learned-proposal form on the 1024 x 8192, S = 48, B = 16384 workload: train the proposal
+    network on generated signals labelled by plain OMP, then time the learned solve next to the
+    dense BF16 solve and the plain FP32 solve on the same batch, and report fallback and
+    support-recovery rates."""
+    import torch
+    from paper_2407_06434_gb300 import omp, proposal as prop
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = gen.get_config(args.config if args.config != WORKLOAD else "gaussian_1024x8192_s48_b16384")
+    A = gen.dictionary(w)
+    Y, sp, planted, _ = gen.signals(w, A)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+    Yd = torch.from_numpy(Y).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    dense = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+    p = omp.Proposal(dense.h, hidden=1024, topk=256, max_batch=w.B, train_batch=4096,
+                     pos_weight=float(w.N - w.S) / w.S, lr=1e-3)
+    W1, b1, W2, b2, beta = prop.init_weights(w.N, 1024, w.S, seed=0, M=w.M)
+    p.set_weights(*[torch.from_numpy(v).to(dev) for v in (W1, b1, W2, b2, beta)])
+    rep = prop.train(dense.h, p, Ad, w, n_signals=args.train_signals, epochs=args.train_epochs,
+                     batch=4096, chunk=w.B)
+    X = torch.empty((w.B, w.S), dtype=torch.float32, device=dev)
+    sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
+    n_iter = torch.empty(w.B, dtype=torch.int32, device=dev)
+    resid = torch.empty(w.B, dtype=torch.float32, device=dev)
+    fb = torch.empty(w.B, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.sum(ms))
+
+    with Clocks(local) as clk:
+        t_learned = timed(lambda: omp.omp_solve_batch_learned(dense.h, p, Ad, Yd, w.S, w.eps, X, sup,
+                                                              n_iter, resid, fb))
+        sup_l, fb_l = sup.cpu().numpy(), fb.cpu().numpy()
+        t_dense = timed(lambda: omp.omp_solve_batch(dense.h, Ad, Yd, w.S, w.eps, X, sup))
+        sup_d = sup.cpu().numpy()
+        plain = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="fp32")
+        t_plain = timed(lambda: omp.omp_solve_batch(plain.h, Ad, Yd, w.S, w.eps, X, sup))
+        sup_p = sup.cpu().numpy()
+    clocks = clk.summary()
+    rec = lambda S_: float(np.mean([set(S_[b][S_[b] >= 0]) == set(planted[b]) for b in range(w.B)]))
+    value = w.B * args.steps / (t_learned / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_learned / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Gaussian dictionary, planted sparse signals)",
+        "config": {"workload": w.name, "form": "learned proposal (top-256) + BF16 fallback",
+                   "M": w.M, "N": w.N, "B": w.B, "S": w.S, "l2": "flushed between timed steps",
+                   "train_signals": args.train_signals, "train_epochs": args.train_epochs},
+        "clocks": clocks,
+        "learned": {"fallback_rate": float(np.mean(fb_l >= 0)),
+                    "mean_fallback_step": float(np.mean(fb_l[fb_l >= 0])) if np.any(fb_l >= 0) else None,
+                    "planted_recovery": rec(sup_l), "support_equal_to_plain": float(np.mean(np.all(sup_l == sup_p, axis=1))),
+                    "train_seconds_data": rep.seconds_data, "train_seconds": rep.seconds_train,
+                    "train_losses": rep.losses},
+        "dense_bf16": {"value": w.B * args.steps / (t_dense / 1e3), "planted_recovery": rec(sup_d)},
+        "plain_fp32": {"value": w.B * args.steps / (t_plain / 1e3), "planted_recovery": rec(sup_p)},
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -355,9 +433,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-signals", type=int, default=64)
+    ap.add_argument("--form", default="dense", choices=["dense", "learned"])
+    ap.add_argument("--train-signals", type=int, default=1 << 20)
+    ap.add_argument("--train-epochs", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

@@ -166,6 +166,118 @@ omp_status omp_correlate_argmax_noalloc(const float* A, const float* R, int64_t 
                                         int64_t B, int32_t* idx_out, float* score_out,
                                         void* stream);
 
+/* omp_solve_batch plus a per-step trace: drop_out (device, B x S float) receives the normalised
+ * residual drop b_k^2 / ||r_{k-1}||^2 of every accepted step k (b_k = q_k^T r_{k-1}, so the drop
+ * is the fraction of the residual energy the step removed), 0 past the signal's last step. Used
+ * to calibrate the learned proposal's residual-drop thresholds. */
+omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                 float eps, float* X_out, int32_t* support_out, float* drop_out,
+                                 void* stream);
+
+/* The descriptor the handle was created with (after defaults) and the device's SM count. */
+omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned proposal. A small network maps the first correlation of a signal,
+ *   x_n = <y, a_n> / (||a_n|| ||y||)                          (BF16 features)
+ * to per-atom logits  o = W2 GELU(W1 x + b1) + b2 + beta |x|  (W1: hidden x N, W2: N x hidden,
+ * BF16 GEMMs with FP32 accumulation, exact GELU, beta a learned scalar: the skip term carries each
+ * atom's own correlation, which a hidden layer much narrower than N cannot pass through), and
+ * proposes the `topk` atoms with the largest logits.
+ * It is trained on the supports that plain OMP picks (omp_solve_batch on generated signals) by
+ * mean binary cross-entropy with logits with a positive-class weight and AdamW on FP32 master
+ * weights; forward and backward run in this library's own kernels. omp_solve_batch_learned then
+ * runs the OMP iteration restricted to the proposed atoms (the projections of Sec. 2.3's D matrix
+ * restricted to the candidates) and sends every signal whose step fails the residual-drop check
+ * b_k^2 / ||r_{k-1}||^2 >= tau_k back to the full correlation from that step on.
+ * The paper has no learned component; plain OMP remains the judge of its results.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct omp_proposal_s* omp_proposal;
+
+typedef struct omp_proposal_desc {
+  int32_t hidden;        /* hidden width, a multiple of 64 (1024) */
+  int32_t topk;          /* candidates per signal, 1..256 (256) */
+  int32_t max_batch;     /* largest inference batch, <= the handle's max_batch */
+  int32_t train_batch;   /* largest training minibatch, a multiple of 64 (4096) */
+  float lr, beta1, beta2, weight_decay, adam_eps;  /* AdamW (1e-3, 0.9, 0.999, 0, 1e-8) */
+  float pos_weight;      /* BCE weight of the positive class, e.g. (N - S) / S */
+} omp_proposal_desc;
+
+void omp_proposal_desc_default(omp_proposal_desc* desc);
+
+/* Create a proposal network for the handle's dictionary shape (N must be a multiple of 64).
+ * Weights start at zero: set them with omp_proposal_set_weights. Thresholds start at 0 (every
+ * restricted step accepted). */
+omp_status omp_proposal_create(omp_handle h, const omp_proposal_desc* desc, omp_proposal* out);
+omp_status omp_proposal_destroy(omp_proposal p);
+
+/* FP32 parameters (device or host pointers): W1 hidden x N row-major, b1 hidden, W2 N x hidden
+ * row-major, b2 N, beta 1. set_weights also resets the optimiser state; get_weights
+ * synchronises. */
+omp_status omp_proposal_set_weights(omp_proposal p, const float* W1, const float* b1, const float* W2,
+                                    const float* b2, const float* beta, void* stream);
+omp_status omp_proposal_get_weights(omp_proposal p, float* W1, float* b1, float* W2, float* b2,
+                                    float* beta, void* stream);
+
+/* One AdamW step on a minibatch: A (device, the handle's dictionary), Y (device, B x M signals),
+ * labels (device, B x S int32 supports, -1 padded). B is a multiple of 64, <= train_batch.
+ * loss_out (device float, may be NULL) receives the minibatch's mean weighted BCE. */
+omp_status omp_proposal_train_step(omp_proposal p, const float* A, const float* Y, const int32_t* labels,
+                                   int64_t B, int32_t S, float* loss_out, void* stream);
+
+/* The same forward and backward pass without the update: gradients of the mean loss (device
+ * pointers, shapes as the parameters; each may be NULL) and the loss. */
+omp_status omp_proposal_gradients(omp_proposal p, const float* A, const float* Y, const int32_t* labels,
+                                  int64_t B, int32_t S, float* dW1, float* db1, float* dW2, float* db2,
+                                  float* dbeta, float* loss_out, void* stream);
+
+/* Inference for B <= max_batch signals: cand_out (device, B x topk int32, ascending atom index)
+ * and optionally the logits (device, B x N float). */
+omp_status omp_proposal_infer(omp_proposal p, const float* A, const float* Y, int64_t B, int32_t* cand_out,
+                              float* logits_out, void* stream);
+
+/* Residual-drop thresholds tau[0..S) (host array). */
+omp_status omp_proposal_set_thresholds(omp_proposal p, const float* tau_host, int32_t S);
+omp_status omp_proposal_get_thresholds(omp_proposal p, float* tau_host, int32_t S);
+
+/* tau_k = the `quantile` (e.g. 0.001) of the positive entries of column k of drops (device,
+ * B x S, from omp_solve_batch_trace on labelled training signals). */
+omp_status omp_proposal_calibrate(omp_proposal p, const float* drops, int64_t B, int32_t S, float quantile,
+                                  void* stream);
+
+/* Per row of a rows x N matrix, the K largest entries' column indices (lowest index first among
+ * equal values), in ascending index order (device pointers). */
+omp_status omp_topk_rows(const float* logits, int64_t rows, int64_t N, int32_t K, int32_t* idx_out,
+                         void* stream);
+
+/* Candidates of the method without the network (for comparison): per signal the topk atoms of
+ * |<y, a_n>| / ||a_n||, ascending atom index (device, B x topk int32). */
+omp_status omp_proposal_baseline_candidates(omp_proposal p, const float* A, const float* Y, int64_t B,
+                                            int32_t* cand_out, void* stream);
+
+/* OMP restricted to given candidate atoms, with the residual-drop fallback to the full correlation:
+ * cand (device, B x K int32, 1 <= K <= 256), tau (device, S float thresholds); other arguments
+ * and results as omp_solve_batch_learned. */
+omp_status omp_solve_batch_candidates(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                      float eps, const int32_t* cand, int32_t K, const float* tau,
+                                      float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                                      float* resid_norm_out, int32_t* fallback_out, void* stream);
+
+/* Generated signals: Y_out (device, B x M) = sum_j coef[b, j] a_{sup[b, j]} + noise_b with A
+ * (device, M x N column-major), sup (device, B x s int32, -1 skipped), coef (device, B x s),
+ * noise (device, B x M, may be NULL). The input model of the problem statement. */
+omp_status omp_synthesize_signals(const float* A, int64_t M, int64_t N, const int32_t* sup,
+                                  const float* coef, const float* noise, int64_t B, int32_t s,
+                                  float* Y_out, void* stream);
+
+/* OMP with the learned proposal: same arguments and results as omp_solve_batch_ex, plus
+ * fallback_out (device, B int32, may be NULL): the step at which the signal left the
+ * candidate-restricted phase for the full correlation, or -1. */
+omp_status omp_solve_batch_learned(omp_handle h, omp_proposal p, const float* A, const float* Y,
+                                   int64_t B, int32_t S, float eps, float* X_out,
+                                   int32_t* support_out, int32_t* n_iter_out,
+                                   float* resid_norm_out, int32_t* fallback_out, void* stream);
+
 /* Read and clear the device error word (OMP_DEVERR_* bits); synchronises the handle's work on
  * `stream` first. Returns OMP_ERR_DEVICE_TIMEOUT if the timeout bit was set, OMP_ERR_NUMERICAL
  * if only the non-finite bit was set, else OMP_OK. */

@@ -326,3 +326,81 @@ def scores(A, r):
     """|<r, a_n>| / ||a_n|| for every atom (FP64), zero-norm atoms scoring 0."""
     A = np.asarray(A, dtype=np.float64)
     return np.abs(A.T @ np.asarray(r, dtype=np.float64)) * _inv_or_zero(atom_norms(A))
+
+
+def omp_candidates_reference(A, y, S, cand, tau, eps=0.0, eps_relative=True):
+    """Alg. 1 with a candidate-restricted start and a residual-drop fallback (FP64, one signal).
+
+    While restricted, step k selects only among the candidate atoms `cand` (lowest atom index on
+    ties) and is accepted if its normalised drop (||r_{k-1}||^2 - ||r_k||^2) / ||r_{k-1}||^2 is at
+    least tau[k] (and the candidate is not dependent and scores above 0). The first rejected step
+    ends the restricted phase: that step and every later one select among all atoms, exactly as
+    Alg. 1. Returns (OmpResult with B = 1, fallback step or -1)."""
+    A = np.asarray(A, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    norms = atom_norms(A)
+    inv = _inv_or_zero(norms)
+    cand = np.asarray(sorted(int(c) for c in cand))
+    res = _empty_result(1, S)
+    y_norm = float(np.linalg.norm(y))
+    res.y_norm[0] = y_norm
+    res.resid_norm[0] = y_norm
+    thr = _threshold(y_norm, eps, eps_relative)
+    if y_norm == 0.0:
+        res.stop[0] = STOP_ZERO
+        return res, -1
+    supp: list[int] = []
+    r = y.copy()
+    x = np.zeros(0)
+    restricted = True
+    fb = -1
+    for k in range(S):
+        while True:
+            if restricted:
+                s = np.abs(A[:, cand].T @ r) * inv[cand]
+                j = int(np.argmax(s))
+                n, sc = int(cand[j]), float(s[j])
+                s2 = np.partition(s, -2)[-2] if s.size > 1 else 0.0
+                margin = (sc - s2) / sc if sc > 0 else 0.0
+            else:
+                n, margin = select(A, inv, r)
+                sc = 1.0
+            a = A[:, n]
+            if supp:
+                As = A[:, supp]
+                dist2 = float(np.sum((a - As @ np.linalg.lstsq(As, a, rcond=None)[0]) ** 2))
+            else:
+                dist2 = float(a @ a)
+            dep = dist2 <= DEPENDENT_RTOL * norms[n] ** 2
+            if restricted:
+                ok = sc > 0 and not dep
+                if ok:
+                    As = A[:, supp + [n]]
+                    xn = np.linalg.lstsq(As, y, rcond=None)[0]
+                    rn = y - As @ xn
+                    drop = (r @ r - rn @ rn) / (r @ r)
+                    ok = drop >= tau[k]
+                if not ok:
+                    restricted = False
+                    fb = k
+                    continue
+            break
+        res.margin[0, k] = margin
+        if dep:
+            res.stop[0] = STOP_DEPENDENT
+            break
+        supp.append(n)
+        As = A[:, supp]
+        x = np.linalg.lstsq(As, y, rcond=None)[0]
+        r = y - As @ x
+        rnn = float(np.linalg.norm(r))
+        res.resid_trace[0, k] = rnn
+        res.n_iter[0] = k + 1
+        res.resid_norm[0] = rnn
+        if rnn <= thr:
+            res.stop[0] = STOP_EPS
+            break
+    kk = len(supp)
+    res.support[0, :kk] = supp
+    res.coef[0, :kk] = x[:kk] if kk else x
+    return res, fb

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int p = blockIdx.x * GPB + grp;
   if (p >= L) return;  // the whole group leaves together
   const int id = ws.live[k & 1][p];
+  const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
   extern __shared__ __align__(16) unsigned char smem[];
   GroupSmem gs = group_smem(smem, grp, ws.Smax);
 
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (wig == 0) {
     const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
     const float* grow = ws.gram + static_cast<size_t>(ns) * ws.N;
-    for (int i = lane; i < k; i += 32) {
+    for (int i = lane; i < kk; i += 32) {
       const int si = supg[i];
       gs.sup[i] = si;
       gs.w[i] = __ldg(grow + si);
@@ -216,19 +217,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     float zl[NB];
 #pragma unroll
     for (int t = 0; t < NB; ++t) zl[t] = 0.f;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < kk; ++i) {
       const float wi = gs.w[i];
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const int j = lane + 32 * t;
-        if (j < k && i <= j) zl[t] = fmaf(Ff[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
+        if (j < kk && i <= j) zl[t] = fmaf(Ff[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
       }
     }
     double zz = 0.0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
       const int j = lane + 32 * t;
-      if (j < k) {
+      if (j < kk) {
         gs.z[j] = zl[t];
         zz += static_cast<double>(zl[t]) * static_cast<double>(zl[t]);
       }
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       float ul[NB];
 #pragma unroll
       for (int t = 0; t < NB; ++t) ul[t] = 0.f;
-      for (int j = 0; j < k; ++j) {
+      for (int j = 0; j < kk; ++j) {
         const float zj = gs.z[j];
         const float* col = Ff + static_cast<size_t>(j) * (j + 1) / 2;
 #pragma unroll
@@ -254,11 +255,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           if (i <= j) ul[t] = fmaf(col[i], zj, ul[t]);
         }
       }
-      const size_t off = static_cast<size_t>(k) * (k + 1) / 2;
+      const size_t off = static_cast<size_t>(kk) * (kk + 1) / 2;
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         const int i = lane + 32 * t;
-        if (i < k) {
+        if (i < kk) {
           const double fv = -gamma * static_cast<double>(ul[t]);
           const float f32 = static_cast<float>(fv);
           Fg[off + i] = fv;
@@ -267,10 +268,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
       if (lane == 0) {
-        Fg[off + k] = gamma;
-        Ff[off + k] = static_cast<float>(gamma);
-        gs.f[k] = static_cast<float>(gamma);
-        gs.sup[k] = ns;
+        Fg[off + kk] = gamma;
+        Ff[off + kk] = static_cast<float>(gamma);
+        gs.f[kk] = static_cast<float>(gamma);
+        gs.sup[kk] = ns;
       }
     }
   }
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   float4 q[V];
 #pragma unroll
   for (int t = 0; t < V; ++t) q[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int na = k + 1;
+  const int na = kk + 1;
   int a = 0;
   for (; a + 2 <= na; a += 2) {
     const float f0 = gs.f[a], f1 = gs.f[a + 1];
@@ -349,9 +350,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     double tot = 0.0;
     for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
     const double rn = sqrt(tot);
-    ws.bv[static_cast<size_t>(id) * ws.Smax + k] = b;
-    ws.sup[static_cast<size_t>(id) * ws.Smax + k] = ns;
-    ws.niter[id] = k + 1;
+    const double rprev = static_cast<double>(ws.rnorm[id]);
+    ws.bv[static_cast<size_t>(id) * ws.Smax + kk] = b;
+    ws.sup[static_cast<size_t>(id) * ws.Smax + kk] = ns;
+    ws.drop[static_cast<size_t>(id) * ws.Smax + kk] =
+        rprev > 0.0 ? static_cast<float>((b * b) / (rprev * rprev)) : 0.f;
+    ws.niter[id] = kk + 1;
     ws.rnorm[id] = static_cast<float>(rn);
     const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ws.ynorm[id])
                                : static_cast<double>(eps);
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (rn <= thr) {
       cont = 0;
       ws.stop[id] = kStopEps;
-    } else if (k + 1 >= S) {
+    } else if (kk + 1 >= S) {
       cont = 0;
       ws.stop[id] = kStopIters;
     }

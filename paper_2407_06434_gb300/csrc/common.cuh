@@ -75,6 +75,8 @@ struct Ws {
   float* rnorm;
   int* niter;
   int* stop;
+  float* drop;     // Bmax x Smax: normalised residual drop b_k^2 / ||r_{k-1}||^2 of each step
+  int* fb;         // Bmax: learned solve, step at which the signal left the restricted phase
   unsigned int* err;
 };
 
@@ -89,6 +91,8 @@ struct CallArgs {
   int* stop;
   int* topk_idx;     // omp_correlate_topk outputs
   float* topk_score;
+  float* drop;       // optional B x S trace of normalised residual drops
+  int* fallback;     // optional B: learned solve fallback step (-1 = none)
 };
 
 __device__ __forceinline__ unsigned long long pack_key(float score, int idx) {
@@ -180,6 +184,17 @@ void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStrea
 void launch_topk_out(const Ws& ws, const CallArgs* args, int B, int topk, cudaStream_t s);
 void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s);
 cudaError_t configure_update_kernels(const Ws& ws);
+
+// learned proposal (restricted.cu, mlp.cu)
+size_t restricted_smem_per_signal(int S, int K, int Mp);
+bool launch_restricted(const Ws& ws, const CallArgs* args, const int* cand, int K, const float* tau,
+                       int B, int S, float eps, int eps_rel, int* fallback, cudaStream_t s);
+const int* proposal_candidates(omp_proposal p);
+int proposal_topk(omp_proposal p);
+const float* proposal_tau(omp_proposal p);
+int proposal_tau_len(omp_proposal p);
+float* proposal_tau_mut(omp_proposal p);
+bool proposal_run_inference(omp_proposal p, const float* A, const float* Y, int B, cudaStream_t s);
 
 // tensor-core correlation (corr_tc.cu)
 struct TcPlan;

@@ -284,6 +284,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
        dalloc(h, &ws.F32, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
        dalloc(h, &ws.sup, Bm * Sm);
+  ok = ok && dalloc(h, &ws.drop, Bm * Sm) && dalloc(h, &ws.fb, Bm);
   ok = ok && dalloc(h, &ws.ynorm, Bm) && dalloc(h, &ws.rnorm, Bm) && dalloc(h, &ws.niter, Bm) &&
        dalloc(h, &ws.stop, Bm) && dalloc(h, &ws.err, 1) && dalloc(h, &h->args_dev, 1);
   ok = ok && dalloc(h, &h->y_stage, Bm * static_cast<size_t>(ws.M)) &&
@@ -349,6 +350,109 @@ omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int6
   st = check_launch();
   if (st != OMP_OK) return st;
   return run_solve(h, static_cast<int>(B), S, eps, s);
+}
+
+omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                 float eps, float* X_out, int32_t* support_out, float* drop_out,
+                                 void* stream) {
+  omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
+  if (st != OMP_OK || !drop_out) return st != OMP_OK ? st : OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A != h->prepared_A) {
+    st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+  }
+  CallArgs a{};
+  a.Y = Y;
+  a.X = X_out;
+  a.support = support_out;
+  a.drop = drop_out;
+  launch_set_args(h->args_dev, a, s);
+  st = check_launch();
+  if (st != OMP_OK) return st;
+  return run_solve(h, static_cast<int>(B), S, eps, s);
+}
+
+namespace {
+omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
+                            omp_proposal p, const int32_t* cand, int32_t K, const float* tau, float* X_out,
+                            int32_t* support_out, int32_t* n_iter_out, float* resid_norm_out,
+                            int32_t* fallback_out, cudaStream_t s);
+}
+
+omp_status omp_solve_batch_candidates(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                      float eps, const int32_t* cand, int32_t K, const float* tau,
+                                      float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                                      float* resid_norm_out, int32_t* fallback_out, void* stream) {
+  omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
+  if (st != OMP_OK) return st;
+  if (!cand || !tau || K < 1 || K > 256 || K > h->d.N) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  return solve_candidates(h, A, Y, B, S, eps, nullptr, cand, K, tau, X_out, support_out, n_iter_out,
+                          resid_norm_out, fallback_out, static_cast<cudaStream_t>(stream));
+}
+
+omp_status omp_solve_batch_learned(omp_handle h, omp_proposal p, const float* A, const float* Y,
+                                   int64_t B, int32_t S, float eps, float* X_out,
+                                   int32_t* support_out, int32_t* n_iter_out,
+                                   float* resid_norm_out, int32_t* fallback_out, void* stream) {
+  omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
+  if (st != OMP_OK) return st;
+  if (!p || S > proposal_tau_len(p)) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  return solve_candidates(h, A, Y, B, S, eps, p, proposal_candidates(p), proposal_topk(p), proposal_tau(p),
+                          X_out, support_out, n_iter_out, resid_norm_out, fallback_out,
+                          static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace {
+// Candidate-restricted OMP followed by the dense loop for the signals that fell back. With a
+// proposal `p`, its inference (features, MLP, top-K) fills `cand` first.
+omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
+                            omp_proposal p, const int32_t* cand, int32_t K, const float* tau, float* X_out,
+                            int32_t* support_out, int32_t* n_iter_out, float* resid_norm_out,
+                            int32_t* fallback_out, cudaStream_t s) {
+  omp_status st;
+  if (A != h->prepared_A) {
+    st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+  }
+  CallArgs a{};
+  a.Y = Y;
+  a.X = X_out;
+  a.support = support_out;
+  a.n_iter = n_iter_out;
+  a.resid = resid_norm_out;
+  a.fallback = fallback_out;
+  launch_set_args(h->args_dev, a, s);
+  const Ws& ws = h->ws;
+  const int b = static_cast<int>(B);
+  launch_init(ws, h->args_dev, b, s);
+  if (p && !proposal_run_inference(p, A, Y, b, s)) return OMP_ERR_CUDA;
+  if (!launch_restricted(ws, h->args_dev, cand, K, tau, b, S, eps, h->d.eps_relative, ws.fb, s))
+    return OMP_ERR_CUDA;
+  // signals that failed the residual-drop check continue in the dense loop
+  launch_compact(ws, 0, b, s);
+  for (int k = 0; k < S; ++k) {
+    enqueue_correlate(h, k, b, s);
+    launch_update(ws, k, b, S, eps, h->d.eps_relative, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, b, s);
+  }
+  launch_finalize(ws, h->args_dev, b, S, s);
+  return check_launch();
+}
+}  // namespace
+
+extern "C" {
+
+omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out) {
+  if (!h) return OMP_ERR_INVALID_ARGUMENT;
+  if (desc_out) *desc_out = h->d;
+  if (sm_count_out) *sm_count_out = h->sm_count;
+  return OMP_OK;
 }
 
 omp_status omp_solve_batch(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,

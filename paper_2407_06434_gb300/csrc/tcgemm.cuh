@@ -1,0 +1,361 @@
+// Persistent tcgen05 GEMM mainloop shared by the correlation (corr_tc.cu) and the learned
+// proposal network (mlp.cu): C = A_op B_op^T with both operands K-major in HBM, loaded by TMA
+// with 128-byte swizzle, multiplied by tcgen05.mma into FP32 accumulators in TMEM, and handed to
+// an epilogue functor 32 columns at a time. C is never written by the mainloop itself.
+//
+// Tiles: 128 rows of A_op (MMA M = the TMEM lanes) x 256 rows of B_op (MMA N = TMEM columns),
+// K in 128-byte stages (64 BF16 or 128 E4M3 elements, 4 MMAs of 32 bytes each per stage).
+// Schedule: units u = s * Tn + t over row tiles s and column tiles t; CTA g of Geff owns the
+// contiguous range [floor(g T / Geff), floor((g + 1) T / Geff)), Geff = min(grid, T / cmin).
+//
+// Roles (192 threads, one CTA per SM):
+//   warp 0 lane 0  TMA producer, 4 stages of 16 KB (A_op) + 32 KB (B_op)
+//   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
+//   warps 2..5     epilogue: tcgen05.ld of 32 columns (the next one in flight), functor call
+// Every mbarrier wait is bounded (about 2 s); a timeout raises OMP_DEVERR_WAIT_TIMEOUT, the
+// roles drain their own copies and MMAs, TMEM is freed and the CTA returns.
+//
+// Epilogue functor interface (one object per epilogue thread, `row` = its TMEM lane 0..127):
+//   void begin(int g, int T, int Geff, int row);
+//   void unit(int s, int t);                              // before the unit's chunks
+//   void chunk(int s, int t, int c0, const uint32_t (&v)[32], float* stage_row);
+//   void end(bool ok);                                    // after the last unit
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace ompk {
+namespace tcg {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int KB = 128;  // K bytes per stage: one 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * KB;
+constexpr int B_BYTES = BN * KB;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int STAGE_ROW = 36;  // floats per staged score row (float4 stores without conflicts)
+constexpr int EPI_STAGE_BYTES = 4 * 32 * STAGE_ROW * 4;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + EPI_STAGE_BYTES;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout (raises the error word and the CTA's abort flag) or when
+// another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(err, OMP_DEVERR_WAIT_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand in 128-byte swizzled rows: 8-row atoms 1024 bytes apart (SBO), version 1,
+// layout SWIZZLE_128B. The K offset inside a row is added to the start address.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(1) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, A/B K-major, N = 256, M = 128;
+// A/B format BF16 (kind::f16) or E4M3 (kind::f8f6f4).
+template <int PREC>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((PREC == OMP_PREC_BF16 ? 1u : 0u) << 7) |
+         ((PREC == OMP_PREC_BF16 ? 1u : 0u) << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
+         (static_cast<uint32_t>(BM >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if (PREC == OMP_PREC_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<PREC>()), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<PREC>()), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Insert (v, n) into a descending top-8; the caller has checked v > s[7]. Equal scores keep
+// the earlier (lower-index) entry in front.
+__device__ __forceinline__ void top8_insert(float (&s)[8], int (&ix)[8], float v, int n) {
+  s[7] = v;
+  ix[7] = n;
+#pragma unroll
+  for (int q = 7; q > 0; --q) {
+    if (s[q] > s[q - 1]) {
+      const float ts = s[q];
+      s[q] = s[q - 1];
+      s[q - 1] = ts;
+      const int ti = ix[q];
+      ix[q] = ix[q - 1];
+      ix[q - 1] = ti;
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------------------- mainloop
+template <int PREC, class Epi>
+__device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtensorMap* tm_b,
+                                          int row_tiles, int col_tiles, int ktiles, int cmin,
+                                          unsigned int* err, Epi& epi) {
+  extern __shared__ uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = row_tiles * col_tiles;
+  if (T <= 0) return;
+  int Geff = T / (cmin > 0 ? cmin : 1);
+  if (Geff < 1) Geff = 1;
+  if (Geff > static_cast<int>(gridDim.x)) Geff = gridDim.x;
+  const int g = blockIdx.x;
+  if (g >= Geff) return;  // uniform across the CTA
+  const int Tn = col_tiles;
+  const int u0 = static_cast<int>(static_cast<long long>(g) * T / Geff);
+  const int u1 = static_cast<int>(static_cast<long long>(g + 1) * T / Geff);
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t bars = base + STAGES * STAGE_BYTES;
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  auto tfull = [&](int a) { return bars + 8u * (2 * STAGES + a); };
+  auto tempty = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
+  const uint32_t drain = bars + 8u * (2 * STAGES + 4);
+  uint8_t* bars_gen = smem_raw + (bars - raw);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * STAGES + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * STAGES + 5) + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull(a), 1);
+      mbar_init(tempty(a), 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(const_cast<uint32_t*>(tmem_slot))),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int kelems = KB / (PREC == OMP_PREC_BF16 ? 2 : 1);  // K elements per stage
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    int stage = 0;
+    uint32_t ph = 0;
+    int last_ph[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) last_ph[s] = -1;
+    bool ok = true;
+    for (int u = u0; u < u1 && ok; ++u) {
+      const int s = u / Tn, t = u - s * Tn;
+      for (int kc = 0; kc < ktiles; ++kc) {
+        if (!mbar_wait(empty(stage), ph ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t dst = base + stage * STAGE_BYTES;
+        mbar_expect_tx(full(stage), STAGE_BYTES);
+        tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
+        tma_load_2d(dst + A_BYTES, tm_b, kc * kelems, t * BN, full(stage));
+        last_ph[stage] = static_cast<int>(ph);
+        if (++stage == STAGES) {
+          stage = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    if (!ok) {
+      // let every copy this thread issued land before the CTA exits
+      volatile int no_abort = 0;
+      for (int s = 0; s < STAGES; ++s)
+        if (last_ph[s] >= 0) mbar_wait(full(s), static_cast<uint32_t>(last_ph[s]), &no_abort, err);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------------ MMA issuer
+    int stage = 0;
+    uint32_t ph = 0;
+    int acc = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int u = u0; u < u1 && ok; ++u) {
+      if (!mbar_wait(tempty(acc), aph ^ 1u, abort_flag, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + static_cast<uint32_t>(acc * BN);
+      for (int kc = 0; kc < ktiles; ++kc) {
+        if (!mbar_wait(full(stage), ph, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = base + stage * STAGE_BYTES;
+        const uint32_t b_addr = a_addr + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma<PREC>(d, sdesc(a_addr + kk * 32), sdesc(b_addr + kk * 32), (kc | kk) != 0);
+        mma_commit(empty(stage));
+        if (++stage == STAGES) {
+          stage = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      mma_commit(tfull(acc));
+      acc ^= 1;
+      if (acc == 0) aph ^= 1u;
+    }
+    // wait until every MMA this thread issued has completed
+    mma_commit(drain);
+    volatile int no_abort = 0;
+    mbar_wait(drain, 0, &no_abort, err);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------------ epilogue
+    const int lg = warp & 3;           // TMEM lane quarter this warp may access
+    const int row = lg * 32 + lane;    // row within the tile
+    float* stage_row = reinterpret_cast<float*>(bars_gen + 256) + ((warp - 2) * 32 + lane) * STAGE_ROW;
+    epi.begin(g, T, Geff, row);
+    int acc = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int u = u0; u < u1; ++u) {
+      const int s = u / Tn, t = u - s * Tn;
+      epi.unit(s, t);
+      if (!mbar_wait(tfull(acc), aph, abort_flag, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) + static_cast<uint32_t>(acc * BN);
+      uint32_t va[32], vb[32];
+      tmem_ld32_issue(taddr, va);
+      tmem_ld_wait();
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t (&cur)[32] = (c & 1) ? vb : va;
+        uint32_t (&nxt)[32] = (c & 1) ? va : vb;
+        if (c + 1 < BN / 32) tmem_ld32_issue(taddr + (c + 1) * 32, nxt);
+        epi.chunk(s, t, c * 32, cur, stage_row);
+        if (c + 1 < BN / 32) tmem_ld_wait();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
+      acc ^= 1;
+      if (acc == 0) aph ^= 1u;
+    }
+    epi.end(ok);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// --------------------------------------------------------------------------- host helpers
+// ld: row stride in elements (0 = kelems)
+bool make_kmajor_map(CUtensorMap* m, const void* ptr, int prec, uint64_t rows, uint64_t kelems,
+                     uint32_t box_rows, uint64_t ld = 0);
+cudaError_t set_smem_attr(const void* kernel);
+
+}  // namespace tcg
+}  // namespace ompk

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, 
     ws.niter[b] = 0;
     ws.stop[b] = alive ? kStopIters : kStopZero;
     ws.flag[b] = alive ? 1 : 0;
+    ws.fb[b] = -1;
     ws.live[1][b] = b;
     if (!finite) atomicOr(ws.err, OMP_DEVERR_NONFINITE);
     if (b == 0) ws.cnt[0] = B;
@@ -184,10 +185,16 @@ __global__ void __launch_bounds__(256) finalize_kernel(Ws ws, const CallArgs* ar
     X[i] = x;
     so[i] = s;
   }
+  if (args->drop) {
+    const float* dg = ws.drop + static_cast<size_t>(b) * ws.Smax;
+    float* dd = args->drop + static_cast<size_t>(b) * S;
+    for (int i = lane; i < S; i += 32) dd[i] = i < n ? dg[i] : 0.f;
+  }
   if (lane == 0) {
     if (args->n_iter) args->n_iter[b] = n;
     if (args->resid) args->resid[b] = ws.rnorm[b];
     if (args->stop) args->stop[b] = ws.stop[b];
+    if (args->fallback) args->fallback[b] = ws.fb[b];
   }
 }
 

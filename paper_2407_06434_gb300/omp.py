@@ -30,7 +30,13 @@ STOP_ITERS, STOP_EPS, STOP_DEPENDENT, STOP_ZERO = 0, 1, 2, 3
 EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_dictionary",
            "omp_solve_batch", "omp_solve_batch_ex", "omp_solve_batch_host", "omp_correlate_topk",
            "omp_get_error", "omp_status_string", "omp_profile_enable", "omp_profile_read",
-           "omp_correlate_argmax_noalloc"]
+           "omp_correlate_argmax_noalloc", "omp_solve_batch_trace", "omp_handle_info",
+           "omp_proposal_desc_default", "omp_proposal_create", "omp_proposal_destroy",
+           "omp_proposal_set_weights", "omp_proposal_get_weights", "omp_proposal_train_step",
+           "omp_proposal_gradients", "omp_proposal_infer", "omp_proposal_set_thresholds",
+           "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
+           "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
+           "omp_synthesize_signals", "omp_solve_batch_learned"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -39,6 +45,13 @@ class omp_desc(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rescore_topk", ctypes.c_int32), ("eps_relative", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class omp_proposal_desc(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("topk", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("train_batch", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("weight_decay", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("pos_weight", ctypes.c_float)]
 
 
 class OmpError(RuntimeError):
@@ -76,6 +89,25 @@ def load(path: Optional[str] = None):
         "omp_profile_enable": (_I32, [_P, _I32]),
         "omp_profile_read": (_I32, [_P, _I32, _P, _P, _P, _P]),
         "omp_correlate_argmax_noalloc": (_I32, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
+        "omp_solve_batch_trace": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P]),
+        "omp_handle_info": (_I32, [_P, ctypes.POINTER(omp_desc), ctypes.POINTER(_I32)]),
+        "omp_proposal_desc_default": (None, [ctypes.POINTER(omp_proposal_desc)]),
+        "omp_proposal_create": (_I32, [_P, ctypes.POINTER(omp_proposal_desc), ctypes.POINTER(_P)]),
+        "omp_proposal_destroy": (_I32, [_P]),
+        "omp_proposal_set_weights": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+        "omp_proposal_get_weights": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+        "omp_proposal_train_step": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
+        "omp_proposal_gradients": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P, _P]),
+        "omp_proposal_infer": (_I32, [_P, _P, _P, _I64, _P, _P, _P]),
+        "omp_proposal_set_thresholds": (_I32, [_P, _P, _I32]),
+        "omp_proposal_get_thresholds": (_I32, [_P, _P, _I32]),
+        "omp_proposal_calibrate": (_I32, [_P, _P, _I64, _I32, _F32, _P]),
+        "omp_topk_rows": (_I32, [_P, _I64, _I64, _I32, _P, _P]),
+        "omp_proposal_baseline_candidates": (_I32, [_P, _P, _P, _I64, _P, _P]),
+        "omp_solve_batch_candidates": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _I32, _P, _P, _P, _P,
+                                              _P, _P, _P]),
+        "omp_synthesize_signals": (_I32, [_P, _I64, _I64, _P, _P, _P, _I64, _I32, _P, _P]),
+        "omp_solve_batch_learned": (_I32, [_P, _P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +265,132 @@ def omp_correlate_argmax_noalloc(A, R, idx_out, score_out, stream=None):
 
 def omp_status_string(status: int) -> str:
     return load().omp_status_string(status).decode()
+
+
+def omp_solve_batch_trace(h: Handle, A, Y, S: int, eps: float, X_out, support_out, drop_out,
+                          stream=None):
+    _check_A(A, h.M, h.N)
+    _check(load().omp_solve_batch_trace(h.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps, _ptr(X_out),
+                                        _ptr(support_out), _ptr(drop_out), _stream(stream)),
+           "omp_solve_batch_trace")
+
+
+def omp_handle_info(h: Handle):
+    d = omp_desc()
+    sms = _I32(0)
+    _check(load().omp_handle_info(h.ptr, ctypes.byref(d), ctypes.byref(sms)), "omp_handle_info")
+    return d, sms.value
+
+
+def omp_synthesize_signals(A, sup, coef, noise, Y_out, stream=None):
+    """Y_out = A[:, sup] coef + noise per row, on the device (A column-major (M, N))."""
+    M, N = A.shape
+    _check(load().omp_synthesize_signals(_ptr(A), M, N, _ptr(sup), _ptr(coef), _ptr(noise),
+                                         sup.shape[0], sup.shape[1], _ptr(Y_out), _stream(stream)),
+           "omp_synthesize_signals")
+
+
+def omp_topk_rows(logits, K: int, idx_out, stream=None):
+    _check(load().omp_topk_rows(_ptr(logits), logits.shape[0], logits.shape[1], K, _ptr(idx_out),
+                                _stream(stream)), "omp_topk_rows")
+
+
+class Proposal:
+    """An ``omp_proposal`` (learned candidate proposal) bound to a handle."""
+
+    def __init__(self, h: Handle, hidden=1024, topk=256, max_batch=None, train_batch=4096,
+                 lr=1e-3, beta1=0.9, beta2=0.999, weight_decay=0.0, adam_eps=1e-8,
+                 pos_weight=1.0):
+        lib = load()
+        d = omp_proposal_desc()
+        lib.omp_proposal_desc_default(ctypes.byref(d))
+        d.hidden, d.topk = hidden, topk
+        d.max_batch = max_batch if max_batch is not None else int(h.desc.max_batch)
+        d.train_batch = train_batch
+        d.lr, d.beta1, d.beta2, d.weight_decay, d.adam_eps = lr, beta1, beta2, weight_decay, adam_eps
+        d.pos_weight = pos_weight
+        ptr = ctypes.c_void_p()
+        _check(lib.omp_proposal_create(h.ptr, ctypes.byref(d), ctypes.byref(ptr)),
+               "omp_proposal_create")
+        self.ptr, self.desc, self.h = ptr, d, h
+
+    def close(self):
+        if self.ptr:
+            load().omp_proposal_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.omp_proposal_destroy(self.ptr)
+            self.ptr = None
+
+    def set_weights(self, W1, b1, W2, b2, beta, stream=None):
+        _check(load().omp_proposal_set_weights(self.ptr, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2),
+                                               _ptr(beta), _stream(stream)),
+               "omp_proposal_set_weights")
+
+    def get_weights(self, W1, b1, W2, b2, beta, stream=None):
+        _check(load().omp_proposal_get_weights(self.ptr, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2),
+                                               _ptr(beta), _stream(stream)),
+               "omp_proposal_get_weights")
+
+    def train_step(self, A, Y, labels, loss_out=None, stream=None):
+        _check(load().omp_proposal_train_step(self.ptr, _ptr(A), _ptr(Y), _ptr(labels), Y.shape[0],
+                                              labels.shape[1], _ptr(loss_out), _stream(stream)),
+               "omp_proposal_train_step")
+
+    def gradients(self, A, Y, labels, dW1=None, db1=None, dW2=None, db2=None, dbeta=None,
+                  loss_out=None, stream=None):
+        _check(load().omp_proposal_gradients(self.ptr, _ptr(A), _ptr(Y), _ptr(labels), Y.shape[0],
+                                             labels.shape[1], _ptr(dW1), _ptr(db1), _ptr(dW2),
+                                             _ptr(db2), _ptr(dbeta), _ptr(loss_out),
+                                             _stream(stream)), "omp_proposal_gradients")
+
+    def infer(self, A, Y, cand_out, logits_out=None, stream=None):
+        _check(load().omp_proposal_infer(self.ptr, _ptr(A), _ptr(Y), Y.shape[0], _ptr(cand_out),
+                                         _ptr(logits_out), _stream(stream)), "omp_proposal_infer")
+
+    def baseline_candidates(self, A, Y, cand_out, stream=None):
+        _check(load().omp_proposal_baseline_candidates(self.ptr, _ptr(A), _ptr(Y), Y.shape[0],
+                                                       _ptr(cand_out), _stream(stream)),
+               "omp_proposal_baseline_candidates")
+
+    def set_thresholds(self, tau):
+        import numpy as np
+        t = np.ascontiguousarray(tau, dtype=np.float32)
+        _check(load().omp_proposal_set_thresholds(self.ptr, t.ctypes.data_as(_P), t.size),
+               "omp_proposal_set_thresholds")
+
+    def get_thresholds(self, S):
+        import numpy as np
+        t = np.zeros(S, dtype=np.float32)
+        _check(load().omp_proposal_get_thresholds(self.ptr, t.ctypes.data_as(_P), S),
+               "omp_proposal_get_thresholds")
+        return t
+
+    def calibrate(self, drops, quantile=1e-3, stream=None):
+        _check(load().omp_proposal_calibrate(self.ptr, _ptr(drops), drops.shape[0], drops.shape[1],
+                                             quantile, _stream(stream)), "omp_proposal_calibrate")
+
+
+def omp_solve_batch_candidates(h: Handle, A, Y, S, eps, cand, tau, X_out, support_out,
+                               n_iter_out=None, resid_norm_out=None, fallback_out=None,
+                               stream=None):
+    _check_A(A, h.M, h.N)
+    _check(load().omp_solve_batch_candidates(h.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps,
+                                             _ptr(cand), cand.shape[1], _ptr(tau), _ptr(X_out),
+                                             _ptr(support_out), _ptr(n_iter_out),
+                                             _ptr(resid_norm_out), _ptr(fallback_out),
+                                             _stream(stream)), "omp_solve_batch_candidates")
+
+
+def omp_solve_batch_learned(h: Handle, p: Proposal, A, Y, S, eps, X_out, support_out,
+                            n_iter_out=None, resid_norm_out=None, fallback_out=None, stream=None):
+    _check_A(A, h.M, h.N)
+    _check(load().omp_solve_batch_learned(h.ptr, p.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps,
+                                          _ptr(X_out), _ptr(support_out), _ptr(n_iter_out),
+                                          _ptr(resid_norm_out), _ptr(fallback_out),
+                                          _stream(stream)), "omp_solve_batch_learned")
 
 
 class OmpSolver:

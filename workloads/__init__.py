@@ -10,5 +10,6 @@ from .gen import (  # noqa: F401
     dictionary,
     planted,
     signals,
-    training_chunk,
+    synthesize,
+    training_batch,
 )

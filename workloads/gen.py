@@ -188,24 +188,49 @@ def signals(w: Workload, A: np.ndarray, seed: int = 0, rows: Optional[slice] = N
     return Y, sp[lo:hi], sup[lo:hi], coef[lo:hi]
 
 
-def training_chunk(w: Workload, A: np.ndarray, chunk_id: int, chunk_size: int, seed: int = 0):
-    """A chunk of training signals drawn like ``w``'s batch but from streams of their own
-    (keyed by ``chunk_id``), so training data never overlaps the evaluation batch."""
+def training_batch(w: Workload, n: int, chunk_id: int, seed: int = 0):
+    """A chunk of training signals drawn like ``w``'s batch from streams of their own (keyed by
+    ``chunk_id``), so training data never overlaps the evaluation batch. Vectorised for large
+    training sets; the measurements are formed from these by ``synthesize`` (host) or on the
+    device (omp_synthesize_signals).
+
+    Returns (support int32 n x s_max (-1 padded), coef float32 n x s_max, noise float32 n x M).
+    Supports are uniform without replacement: the first s distinct values of a row of uniform
+    draws, which is a uniform random s-subset in random order."""
     rng = _rng(seed, _S_TRAIN, chunk_id)
+    s_max = w.s_max
     if w.s_min == w.s_max:
-        sp = np.full(chunk_size, w.s_max, dtype=np.int32)
+        sp = np.full(n, s_max, dtype=np.int32)
     else:
-        sp = rng.integers(w.s_min, w.s_max + 1, size=chunk_size).astype(np.int32)
-    sup = np.full((chunk_size, w.s_max), -1, dtype=np.int64)
-    for b in range(chunk_size):
-        sup[b, : sp[b]] = rng.choice(w.N, size=int(sp[b]), replace=False)
+        sp = rng.integers(w.s_min, w.s_max + 1, size=n).astype(np.int32)
+    m = s_max + 32
+    draws = rng.integers(0, w.N, size=(n, m))
+    order = np.argsort(draws, axis=1, kind="stable")
+    srt = np.take_along_axis(draws, order, axis=1)
+    dup_sorted = np.zeros_like(srt, dtype=bool)
+    dup_sorted[:, 1:] = srt[:, 1:] == srt[:, :-1]
+    dup = np.zeros_like(dup_sorted)
+    np.put_along_axis(dup, order, dup_sorted, axis=1)
+    keep = ~dup
+    rank = np.cumsum(keep, axis=1)
+    if np.any(rank[:, -1] < s_max):
+        raise RuntimeError("too many repeated draws; enlarge the draw width")
+    sel = keep & (rank <= s_max)
+    sup = draws[sel].reshape(n, s_max).astype(np.int32)
+    sup[np.arange(s_max)[None, :] >= sp[:, None]] = -1
     if w.coef_kind == "normal":
-        coef = rng.standard_normal((chunk_size, w.s_max))
+        coef = rng.standard_normal((n, s_max), dtype=np.float32)
     else:
-        coef = rng.uniform(0.5, 1.0, size=(chunk_size, w.s_max))
-        coef *= np.where(rng.integers(0, 2, size=coef.shape) == 0, -1.0, 1.0)
-    coef[np.arange(w.s_max)[None, :] >= sp[:, None]] = 0.0
-    noise = rng.standard_normal((chunk_size, w.M)) * w.sigma if w.sigma else \
-        np.zeros((chunk_size, w.M))
-    Y = _synthesise(A, sup, coef, noise)
-    return Y, sp, sup, coef
+        coef = rng.uniform(0.5, 1.0, size=(n, s_max)).astype(np.float32)
+        coef *= np.where(rng.integers(0, 2, size=coef.shape) == 0, -1.0, 1.0).astype(np.float32)
+    coef[sup < 0] = 0.0
+    if w.sigma:
+        noise = rng.standard_normal((n, w.M), dtype=np.float32) * np.float32(w.sigma)
+    else:
+        noise = np.zeros((n, w.M), dtype=np.float32)
+    return sup, coef, noise
+
+
+def synthesize(A: np.ndarray, sup: np.ndarray, coef: np.ndarray, noise: np.ndarray):
+    """y = A[:, sup] coef + noise per row, in FP64 on the FP32 dictionary, rounded to FP32."""
+    return _synthesise(A, sup.astype(np.int64), coef.astype(np.float64), noise.astype(np.float64))

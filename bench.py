@@ -166,6 +166,7 @@ def run_gpu(args):
         X = torch.empty((w.B, w.S), dtype=torch.float32, device=dev)
         sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
         omp.omp_prepare_dictionary(h, Ad)
+        tuned = omp.omp_autotune(h, Ad, Yd, w.S, w.eps, repeats=2)
         for _ in range(args.warmup):
             omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
         torch.cuda.synchronize()
@@ -214,7 +215,7 @@ def run_gpu(args):
             t0 = time.perf_counter()
             omp.omp_solve_batch_host(h, Ad, Yh, w.S, w.eps, Xh, Sh)
             e2e_t.append(time.perf_counter() - t0)
-        res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live,
+        res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live, update_warps=tuned,
                    e2e_s=float(np.sum(e2e_t)), e2e_steps=len(e2e_t),
                    sup=sup.cpu().numpy(), X=X.cpu().numpy())
         solver.close()
@@ -281,6 +282,7 @@ def run_gpu(args):
         "data": "synthetic (seeded Gaussian dictionary and planted sparse signals)",
         "config": {"workload": w.name, "M": w.M, "N": w.N, "B": w.B, "S": w.S,
                    "precision": args.precision, "rescore_topk": topk,
+                   "update_warps_per_signal": chosen["update_warps"],
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": clocks,

@@ -174,6 +174,15 @@ omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, i
                                  float eps, float* X_out, int32_t* support_out, float* drop_out,
                                  void* stream);
 
+/* Autotuner: times `repeats` solves of (A, Y, B, S, eps) for every valid launch shape of the
+ * append/update kernel (1, 2, 4 or 8 warps per signal for the padded signal length) and keeps
+ * the fastest on the handle; *choice_out (may be NULL) receives the warps per signal. If the
+ * environment variable OMP_AUTOTUNE_CACHE names a file, a choice recorded there for the same GPU,
+ * M, N, precision, B and S is used without timing, and new choices are appended to it.
+ * Synchronises `stream`. Captured graphs are dropped when the choice changes. */
+omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
+                        int32_t repeats, int32_t* choice_out, void* stream);
+
 /* The descriptor the handle was created with (after defaults) and the device's SM count. */
 omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out);
 

@@ -23,7 +23,8 @@ namespace ompk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlk = 8;  // z blocks of 32 columns: Smax <= 256 (NB <= kMaxBlk per kernel)
+constexpr int kMaxBlk = 8;  // lane slots of 32 rows/columns of F: Smax <= 256
+constexpr int kTriMax = 64;  // the packed FP32 factor is staged in shared memory for Smax <= 64
 
 __device__ __forceinline__ void group_sync(int W, int grp) {
   if (W == 1)
@@ -47,17 +48,24 @@ struct GroupSmem {
   int* cidx;     // 8
   double* part;  // 16: per-warp partials of b and ||r||^2
   int* scal;     // 4: n*, dependent flag
+  float* tri;    // Smax (Smax + 1) / 2 when Smax <= kTriMax: staged copy of the packed FP32 F
 };
+
+__host__ __device__ __forceinline__ size_t tri_floats(int Smax) {
+  return Smax <= kTriMax ? static_cast<size_t>(Smax) * (Smax + 1) / 2 : 0;
+}
 
 __host__ __device__ __forceinline__ size_t group_bytes(int Smax) {
   const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
-                   8 * 4 + 16 * 8 + 16;
+                   8 * 4 + 16 * 8 + 16 + (tri_floats(Smax) * 4 + 15) / 16 * 16;
   return (b + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, int Smax) {
   unsigned char* g = base + grp * group_bytes(Smax);
   GroupSmem s;
+  s.tri = reinterpret_cast<float*>(g);  // first, so it is 16-byte aligned
+  g += (tri_floats(Smax) * 4 + 15) / 16 * 16;
   s.part = reinterpret_cast<double*>(g);
   s.f = reinterpret_cast<float*>(g + 16 * 8);
   s.sup = reinterpret_cast<int*>(s.f + Smax + 1);
@@ -69,7 +77,76 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, in
   return s;
 }
 
-template <int W, int V, int NB>
+// New inverse-Cholesky column for a support of kk atoms, run by one warp: lane slot j = lane + 32 t
+// for t < NB covers the kk <= 32 NB rows/columns of F (NB is the smallest power of two that fits,
+// so early iterations issue no predicated-off work). Fr is where the current factor is read (a
+// shared-memory copy or F itself); the new column goes to Ff (FP32) and Fg (FP64).
+template <int NB>
+__device__ __forceinline__ void append_column(const Ws& ws, const GroupSmem& gs, const float* Fr,
+                                              float* Ff, double* Fg, int kk, int ns, int lane) {
+  // z_j = sum_{i<=j} F[i,j] w_i
+  float zl[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) zl[t] = 0.f;
+  for (int i = 0; i < kk; ++i) {
+    const float wi = gs.w[i];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int j = lane + 32 * t;
+      if (j < kk && i <= j) zl[t] = fmaf(Fr[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
+    }
+  }
+  double zz = 0.0;
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int j = lane + 32 * t;
+    if (j < kk) {
+      gs.z[j] = zl[t];
+      zz += static_cast<double>(zl[t]) * static_cast<double>(zl[t]);
+    }
+  }
+  zz = warp_sum(zz);
+  const double nrm2 = ws.norm2[ns];
+  const double delta = nrm2 - zz;
+  const bool dep = !(delta > kDepRtol * nrm2);
+  if (lane == 0) gs.scal[1] = dep ? 1 : 0;
+  __syncwarp();
+  if (dep) return;
+  const double gamma = 1.0 / sqrt(delta);
+  // u_i = sum_{j>=i} F[i,j] z_j, lane slot i; one coalesced column per j
+  float ul[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) ul[t] = 0.f;
+  for (int j = 0; j < kk; ++j) {
+    const float zj = gs.z[j];
+    const float* col = Fr + static_cast<size_t>(j) * (j + 1) / 2;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int i = lane + 32 * t;
+      if (i <= j) ul[t] = fmaf(col[i], zj, ul[t]);
+    }
+  }
+  const size_t off = static_cast<size_t>(kk) * (kk + 1) / 2;
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int i = lane + 32 * t;
+    if (i < kk) {
+      const double fv = -gamma * static_cast<double>(ul[t]);
+      const float f32 = static_cast<float>(fv);
+      Fg[off + i] = fv;
+      Ff[off + i] = f32;
+      gs.f[i] = f32;
+    }
+  }
+  if (lane == 0) {
+    Fg[off + kk] = gamma;
+    Ff[off + kk] = static_cast<float>(gamma);
+    gs.f[kk] = static_cast<float>(gamma);
+    gs.sup[kk] = ns;
+  }
+}
+
+template <int W, int V>
 __global__ void __launch_bounds__(kThreads, 2)
     append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
   const bool top1 = ws.prec == OMP_PREC_FP32;
@@ -83,6 +160,25 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
   extern __shared__ __align__(16) unsigned char smem[];
   GroupSmem gs = group_smem(smem, grp, ws.Smax);
+
+  // Loads that do not depend on the selection go out first: the packed FP32 factor (staged in
+  // shared memory with 16-byte loads, so the serial z and F z loops wait on no global load), the
+  // support, and the norms used at the end.
+  float* Ff = ws.F32 + static_cast<size_t>(id) * ws.Fstride;
+  const bool staged = ws.Smax <= kTriMax;
+  if (wig == 0) {
+    if (staged) {
+      const int tn4 = (kk * (kk + 1) / 2 + 3) >> 2;  // within the padded stride
+      const float4* src = reinterpret_cast<const float4*>(Ff);
+      float4* dst = reinterpret_cast<float4*>(gs.tri);
+#pragma unroll 4
+      for (int e = lane; e < tn4; e += 32) dst[e] = src[e];
+    }
+    const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
+    for (int i = lane; i < kk; i += 32) gs.sup[i] = supg[i];
+  }
+  const float rprev = ws.rnorm[id];
+  const float ynorm = ws.ynorm[id];
 
   const int M4 = ws.Mp >> 2;
   const float4* rrow = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
@@ -148,23 +244,30 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     group_sync(W, grp);
-    // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row
-    for (int c = 0; c < ws.topk; ++c) {
-      const int n = gs.cidx[c];
-      float acc = 0.f;
-      if (n >= 0) {
-        const float4* a4 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n) * ws.Mp);
+    // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
+    // candidates per pass so their row loads are in flight together
+    for (int c = 0; c < ws.topk; c += 2) {
+      const int n0 = gs.cidx[c];
+      const int n1 = c + 1 < ws.topk ? gs.cidx[c + 1] : -1;
+      const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n0 < 0 ? 0 : n0) * ws.Mp);
+      const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n1 < 0 ? 0 : n1) * ws.Mp);
+      float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-        for (int t = 0; t < V; ++t) {
-          const int s = t * (W * 32) + wig * 32 + lane;
-          if (s < M4) {
-            const float4 a = __ldg(a4 + s);
-            acc += a.x * r[t].x + a.y * r[t].y + a.z * r[t].z + a.w * r[t].w;
-          }
+      for (int t = 0; t < V; ++t) {
+        const int s = t * (W * 32) + wig * 32 + lane;
+        if (s < M4) {
+          const float4 x0 = n0 >= 0 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 x1 = n1 >= 0 ? __ldg(a1 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+          acc0 += x0.x * r[t].x + x0.y * r[t].y + x0.z * r[t].z + x0.w * r[t].w;
+          acc1 += x1.x * r[t].x + x1.y * r[t].y + x1.z * r[t].z + x1.w * r[t].w;
         }
       }
-      acc = warp_sum_f(acc);
-      if (lane == 0) gs.cpart[c * 8 + wig] = acc;
+      acc0 = warp_sum_f(acc0);
+      acc1 = warp_sum_f(acc1);
+      if (lane == 0) {
+        gs.cpart[c * 8 + wig] = acc0;
+        if (c + 1 < ws.topk) gs.cpart[(c + 1) * 8 + wig] = acc1;
+      }
     }
     group_sync(W, grp);
     if (wig == 0) {
@@ -203,77 +306,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   // so FP64 arithmetic there would add no accuracy. The Schur complement delta, gamma and the
   // stored factor (used by the back-substitution) are FP64.
   double* Fg = ws.F + static_cast<size_t>(id) * ws.Fstride;
-  float* Ff = ws.F32 + static_cast<size_t>(id) * ws.Fstride;
   if (wig == 0) {
-    const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
+    __syncwarp();  // the support and the staged factor are visible to the whole warp
     const float* grow = ws.gram + static_cast<size_t>(ns) * ws.N;
-    for (int i = lane; i < kk; i += 32) {
-      const int si = supg[i];
-      gs.sup[i] = si;
-      gs.w[i] = __ldg(grow + si);
-    }
+    for (int i = lane; i < kk; i += 32) gs.w[i] = __ldg(grow + gs.sup[i]);
     __syncwarp();
-    // z_j = sum_{i<=j} F[i,j] w_i, lane slot j = lane + 32 t
-    float zl[NB];
-#pragma unroll
-    for (int t = 0; t < NB; ++t) zl[t] = 0.f;
-    for (int i = 0; i < kk; ++i) {
-      const float wi = gs.w[i];
-#pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        const int j = lane + 32 * t;
-        if (j < kk && i <= j) zl[t] = fmaf(Ff[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
-      }
-    }
-    double zz = 0.0;
-#pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int j = lane + 32 * t;
-      if (j < kk) {
-        gs.z[j] = zl[t];
-        zz += static_cast<double>(zl[t]) * static_cast<double>(zl[t]);
-      }
-    }
-    zz = warp_sum(zz);
-    const double nrm2 = ws.norm2[ns];
-    const double delta = nrm2 - zz;
-    const bool dep = !(delta > kDepRtol * nrm2);
-    if (lane == 0) gs.scal[1] = dep ? 1 : 0;
-    __syncwarp();
-    if (!dep) {
-      const double gamma = 1.0 / sqrt(delta);
-      // u_i = sum_{j>=i} F[i,j] z_j, lane slot i; one coalesced column per j
-      float ul[NB];
-#pragma unroll
-      for (int t = 0; t < NB; ++t) ul[t] = 0.f;
-      for (int j = 0; j < kk; ++j) {
-        const float zj = gs.z[j];
-        const float* col = Ff + static_cast<size_t>(j) * (j + 1) / 2;
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          const int i = lane + 32 * t;
-          if (i <= j) ul[t] = fmaf(col[i], zj, ul[t]);
-        }
-      }
-      const size_t off = static_cast<size_t>(kk) * (kk + 1) / 2;
-#pragma unroll
-      for (int t = 0; t < NB; ++t) {
-        const int i = lane + 32 * t;
-        if (i < kk) {
-          const double fv = -gamma * static_cast<double>(ul[t]);
-          const float f32 = static_cast<float>(fv);
-          Fg[off + i] = fv;
-          Ff[off + i] = f32;
-          gs.f[i] = f32;
-        }
-      }
-      if (lane == 0) {
-        Fg[off + kk] = gamma;
-        Ff[off + kk] = static_cast<float>(gamma);
-        gs.f[kk] = static_cast<float>(gamma);
-        gs.sup[kk] = ns;
-      }
-    }
+    const float* Fr = staged ? gs.tri : Ff;
+    const int nb = (kk + 31) >> 5;
+    if (nb <= 1) append_column<1>(ws, gs, Fr, Ff, Fg, kk, ns, lane);
+    else if (nb <= 2) append_column<2>(ws, gs, Fr, Ff, Fg, kk, ns, lane);
+    else if (nb <= 4) append_column<4>(ws, gs, Fr, Ff, Fg, kk, ns, lane);
+    else append_column<8>(ws, gs, Fr, Ff, Fg, kk, ns, lane);
   }
   group_sync(W, grp);
   if (gs.scal[1]) {
@@ -350,14 +393,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     double tot = 0.0;
     for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
     const double rn = sqrt(tot);
-    const double rprev = static_cast<double>(ws.rnorm[id]);
+    const double rp = static_cast<double>(rprev);
     ws.bv[static_cast<size_t>(id) * ws.Smax + kk] = b;
     ws.sup[static_cast<size_t>(id) * ws.Smax + kk] = ns;
     ws.drop[static_cast<size_t>(id) * ws.Smax + kk] =
-        rprev > 0.0 ? static_cast<float>((b * b) / (rprev * rprev)) : 0.f;
+        rp > 0.0 ? static_cast<float>((b * b) / (rp * rp)) : 0.f;
     ws.niter[id] = kk + 1;
     ws.rnorm[id] = static_cast<float>(rn);
-    const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ws.ynorm[id])
+    const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ynorm)
                                : static_cast<double>(eps);
     int cont = 1;
     if (rn <= thr) {
@@ -371,35 +414,70 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// W warps per signal and V float4 slots per lane cover Mp <= 128 W V; NB blocks of 32 columns
-// cover Smax <= 32 NB.
-template <int W, int V, int NB>
+// W warps per signal and V float4 slots per lane cover Mp <= 128 W V.
+template <int W, int V>
 void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
   constexpr int GPB = 8 / W;
   const size_t smem = group_bytes(ws.Smax) * GPB;
-  append_update_kernel<W, V, NB><<<(B + GPB - 1) / GPB, kThreads, smem, s>>>(ws, k, S, eps, eps_rel);
+  append_update_kernel<W, V><<<(B + GPB - 1) / GPB, kThreads, smem, s>>>(ws, k, S, eps, eps_rel);
 }
 
-template <int NB>
-void launch_nb(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  if (ws.Mp <= 256) launch_t<1, 2, NB>(ws, k, B, S, eps, eps_rel, s);
-  else if (ws.Mp <= 1024) launch_t<1, 8, NB>(ws, k, B, S, eps, eps_rel, s);
-  else if (ws.Mp <= 2048) launch_t<2, 8, NB>(ws, k, B, S, eps, eps_rel, s);
-  else if (ws.Mp <= 4096) launch_t<4, 8, NB>(ws, k, B, S, eps, eps_rel, s);
-  else launch_t<8, 8, NB>(ws, k, B, S, eps, eps_rel, s);
+template <int W>
+void launch_w(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  if (V == 1) launch_t<W, 1>(ws, k, B, S, eps, eps_rel, s);
+  else if (V == 2) launch_t<W, 2>(ws, k, B, S, eps, eps_rel, s);
+  else if (V == 4) launch_t<W, 4>(ws, k, B, S, eps, eps_rel, s);
+  else launch_t<W, 8>(ws, k, B, S, eps, eps_rel, s);
+}
+
+template <int W, int V>
+cudaError_t set_attr_t(int bytes) {
+  return cudaFuncSetAttribute(append_update_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+template <int W>
+cudaError_t set_attr_w(const Ws& ws) {
+  const int bytes = static_cast<int>(group_bytes(ws.Smax) * (8 / W));
+  cudaError_t e = set_attr_t<W, 1>(bytes);
+  if (e == cudaSuccess) e = set_attr_t<W, 2>(bytes);
+  if (e == cudaSuccess) e = set_attr_t<W, 4>(bytes);
+  if (e == cudaSuccess) e = set_attr_t<W, 8>(bytes);
+  return e;
 }
 
 }  // namespace
 
 cudaError_t configure_update_kernels(const Ws& ws) {
   if (ws.Mp > 8192 || ws.Smax > 32 * kMaxBlk) return cudaErrorInvalidValue;
-  return cudaSuccess;
+  cudaError_t e = set_attr_w<1>(ws);
+  if (e == cudaSuccess) e = set_attr_w<2>(ws);
+  if (e == cudaSuccess) e = set_attr_w<4>(ws);
+  if (e == cudaSuccess) e = set_attr_w<8>(ws);
+  return e;
+}
+
+// float4 slots per lane for W warps per signal (a power of two, 0 if more than 8 are needed)
+int update_slots(int Mp, int W) {
+  const int need = (Mp + 128 * W - 1) / (128 * W);
+  int V = 1;
+  while (V < need) V <<= 1;
+  return V <= 8 ? V : 0;
+}
+
+int update_default_warps(int Mp) {
+  for (int W = 1; W <= 8; W <<= 1)
+    if (update_slots(Mp, W)) return W;
+  return 0;
 }
 
 void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  if (ws.Smax <= 32) launch_nb<1>(ws, k, B, S, eps, eps_rel, s);
-  else if (ws.Smax <= 128) launch_nb<4>(ws, k, B, S, eps, eps_rel, s);
-  else launch_nb<8>(ws, k, B, S, eps, eps_rel, s);
+  const int W = ws.upd_w;
+  const int V = update_slots(ws.Mp, W);
+  if (W == 1) launch_w<1>(ws, V, k, B, S, eps, eps_rel, s);
+  else if (W == 2) launch_w<2>(ws, V, k, B, S, eps, eps_rel, s);
+  else if (W == 4) launch_w<4>(ws, V, k, B, S, eps, eps_rel, s);
+  else launch_w<8>(ws, V, k, B, S, eps, eps_rel, s);
 }
 
 }  // namespace ompk

@@ -36,6 +36,7 @@ constexpr int kMpAlign = 64;          // M padding (x2 for E4M3): one 128-byte K
 constexpr int kSigTile = 128;         // signals per correlation tile (TMEM lanes)
 constexpr int kMaxTopk = 8;
 constexpr int kPieces = 32;           // candidate slots per position (quantised paths)
+constexpr int kTcParts = 2;           // candidate lists per signal and correlation CTA
 constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a||^2
 constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
 
@@ -47,7 +48,8 @@ struct Ws {
   int tc_grid;     // tensor-core correlation: persistent grid size
   int tc_tn;       // atom tiles of 256
   int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
-  int64_t Fstride; // Smax (Smax + 1) / 2
+  int upd_w;       // append/update kernel: warps per signal (1, 2, 4, 8; autotuned)
+  int64_t Fstride; // Smax (Smax + 1) / 2 rounded up to a multiple of 4
   // dictionary
   float* A32;
   __nv_bfloat16* A16;
@@ -163,12 +165,13 @@ __host__ __device__ __forceinline__ int tc_start(int g, int T, int Geff) {
 __host__ __device__ __forceinline__ int tc_owner(int u, int T, int Geff) {
   return static_cast<int>((static_cast<long long>(u + 1) * Geff - 1) / T);
 }
-// candidate slots [0, count) of live position p hold its signal tile's pieces
+// candidate slots [0, count) of live position p hold its signal tile's lists: kTcParts per
+// piece (one per part of the atom columns of each unit)
 __device__ __forceinline__ int tc_piece_count(const Ws& ws, int L, int p) {
   int T, Geff;
   tc_sched(L, ws.tc_grid, ws.tc_tn, ws.tc_cmin, T, Geff);
   const int s = p / kSigTile;
-  return tc_owner(s * ws.tc_tn + ws.tc_tn - 1, T, Geff) - tc_owner(s * ws.tc_tn, T, Geff) + 1;
+  return kTcParts * (tc_owner(s * ws.tc_tn + ws.tc_tn - 1, T, Geff) - tc_owner(s * ws.tc_tn, T, Geff) + 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -184,6 +187,8 @@ void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStrea
 void launch_topk_out(const Ws& ws, const CallArgs* args, int B, int topk, cudaStream_t s);
 void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s);
 cudaError_t configure_update_kernels(const Ws& ws);
+int update_slots(int Mp, int W);
+int update_default_warps(int Mp);
 
 // learned proposal (restricted.cu, mlp.cu)
 size_t restricted_smem_per_signal(int S, int K, int Mp);

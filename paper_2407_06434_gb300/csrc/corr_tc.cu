@@ -9,9 +9,10 @@
 // atoms in ascending order with a strict '>' so that the lowest index keeps a tie. The update
 // kernel merges the pieces' lists and rescores the best 8 in FP32.
 //
-// A CTA flushes its list for signal tile s into candidate slot g - owner(s * Tn), so a tile's
-// lists occupy consecutive slots; the mainloop's minimum units per CTA (`cmin`) bounds the
-// pieces per tile by kPieces.
+// The EPI_PARTS epilogue warps of a lane quarter see different column parts of each unit, so each
+// keeps its own list; a CTA flushes them for signal tile s into candidate slots
+// EPI_PARTS (g - owner(s * Tn)) + part, so a tile's lists occupy consecutive slots; the
+// mainloop's minimum units per CTA (`cmin`) bounds the pieces per tile by kPieces / EPI_PARTS.
 #include "tcgemm.cuh"
 
 namespace ompk {
@@ -60,12 +61,26 @@ namespace {
 using namespace tcg;
 
 // Running top-8 per signal; flushed when the CTA moves to another signal tile and at the end.
+// The column scales of the warp's EPI_COLS columns are staged in its shared scratch at each
+// unit, and those of the next column tile are loaded meanwhile, so no chunk waits on a global
+// load.
+//
+// The EPI_PARTS threads of a row (one per part of the columns) publish their 8th-best score,
+// tagged with the signal tile, in shared slots. A score below another part's 8th best is beaten
+// by 8 scores of the same row, so it cannot be in the row's top 8 and is not inserted; the lists
+// are then no longer each part's own top 8, but their union still holds the row's top 8, which
+// is all the merge downstream needs. A stale value (the slots are read without a barrier) is
+// smaller and only prunes less; a value tagged with another tile is ignored.
 struct EpiTop8 {
   Ws ws;
   int L;
-  int g, T, Geff, row, cur_s;
+  int g, T, Geff, row, part, cur_s;
   float ts[8];
   int ti[8];
+  float* scr;
+  unsigned long long* peers;
+  float4 pf;  // prefetched scales of column tile pf_t (this lane's 4 of the warp's 128)
+  int pf_t;
 
   __device__ void reset() {
 #pragma unroll
@@ -78,58 +93,94 @@ struct EpiTop8 {
     const int p = s * BM + row;
     if (p >= L) return;
     const int piece = g - tc_owner(s * ws.tc_tn, T, Geff);
-    const size_t off = (static_cast<size_t>(p) * ws.pieces + piece) * kMaxTopk;
+    const size_t off =
+        (static_cast<size_t>(p) * ws.pieces + EPI_PARTS * piece + part) * kMaxTopk;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       ws.cand_s[off + q] = ts[q];
       ws.cand_i[off + q] = ti[q];
     }
   }
-  __device__ void begin(int g_, int T_, int Geff_, int row_) {
+  // this lane's EPI_COLS / 32 consecutive scales of the warp's columns of tile t
+  __device__ float4 load_scales(int t) const {
+    static_assert(EPI_COLS == 128, "one float4 per lane");
+    return __ldg(reinterpret_cast<const float4*>(ws.escale + t * BN + part * EPI_COLS) + (row & 31));
+  }
+  __device__ void begin(int g_, int T_, int Geff_, int row_, int part_, float* scratch,
+                        unsigned long long* peers_) {
+    scr = scratch;
+    peers = peers_;
+    pf_t = -1;
     g = g_;
     T = T_;
     Geff = Geff_;
     row = row_;
+    part = part_;
     cur_s = -1;
     reset();
   }
-  __device__ void unit(int s, int) {
+  __device__ void unit(int s, int t) {
     if (s != cur_s) {
       if (cur_s >= 0) flush(cur_s);
       cur_s = s;
       reset();
     }
+    const float4 v = pf_t == t ? pf : load_scales(t);
+    __syncwarp();  // every lane has finished with the previous unit's scales
+    reinterpret_cast<float4*>(scr)[row & 31] = v;
+    __syncwarp();
+    pf_t = t + 1 < ws.tc_tn ? t + 1 : 0;  // the next unit's column tile (units run t-major)
+    pf = load_scales(pf_t);
   }
-  // Scores of a 32-column chunk go to this lane's row of the staging buffer; a compare-only
-  // pass marks the columns above the current 8th score, and only those are inserted (few per
-  // chunk once the list is warm), so the warp does not diverge per column.
-  __device__ void chunk(int, int t, int c0, const uint32_t (&cur)[32], float* stage_row) {
+  // A compare-only pass marks the columns whose score beats the threshold; only those are
+  // inserted (few per chunk once the list is warm), each read back from the registers with a
+  // select tree, so the warp neither diverges per column nor needs a staging buffer. A fresh list
+  // takes the chunk's first 8 columns unconditionally: the smallest of them is a safe threshold
+  // for the rest (at least 8 scores of the chunk reach it).
+  __device__ void chunk(int, int t, int c0, const uint32_t (&cur)[32]) {
     const int nb = t * BN + c0;
     const int lim = min(32, ws.N - nb);
-    const float4* sc4 = reinterpret_cast<const float4*>(ws.escale + nb);
-    const float thr = ts[7];
+    const float* scl = scr + (c0 - part * EPI_COLS);
+    const float4* sc4 = reinterpret_cast<const float4*>(scl);
+    int j0 = 0;
+    if (ti[0] < 0) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float v = fabsf(__uint_as_float(cur[j])) * scl[j];
+        if (j < lim && v > ts[7]) top8_insert(ts, ti, v, nb + j);  // false only for NaN
+      }
+      j0 = 8;
+    }
+    // own 8th best, raised to just below each other part's when that one is positive and
+    // belongs to the same signal tile (x >= other  <=>  x > its predecessor, for x >= 0)
+    float thr = ts[7];
+#pragma unroll
+    for (int o = 1; o < EPI_PARTS; ++o) {
+      const int q = (part + o) % EPI_PARTS;
+      const unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(peers + q * BM + row);
+      const float othr = __uint_as_float(static_cast<uint32_t>(v));
+      if (static_cast<int>(v >> 32) == cur_s && othr > 0.f)
+        thr = fmaxf(thr, __uint_as_float(__float_as_uint(othr) - 1u));
+    }
     uint32_t mask = 0;
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
-      const float4 sc = __ldg(sc4 + j4);
-      float4 o;
-      o.x = fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x;
-      o.y = fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y;
-      o.z = fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z;
-      o.w = fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w;
-      mask |= (o.x > thr ? 1u : 0u) << (4 * j4 + 0);
-      mask |= (o.y > thr ? 1u : 0u) << (4 * j4 + 1);
-      mask |= (o.z > thr ? 1u : 0u) << (4 * j4 + 2);
-      mask |= (o.w > thr ? 1u : 0u) << (4 * j4 + 3);
-      *reinterpret_cast<float4*>(stage_row + 4 * j4) = o;
+      const float4 sc = sc4[j4];
+      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x > thr ? 1u : 0u) << (4 * j4 + 0);
+      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y > thr ? 1u : 0u) << (4 * j4 + 1);
+      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z > thr ? 1u : 0u) << (4 * j4 + 2);
+      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w > thr ? 1u : 0u) << (4 * j4 + 3);
     }
     if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
+    if (j0) mask &= 0xffffff00u;
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      const float score = stage_row[j];
+      const float score = fabsf(__uint_as_float(pick32(cur, j))) * scl[j];
       if (score > ts[7]) top8_insert(ts, ti, score, nb + j);
     }
+    *reinterpret_cast<volatile unsigned long long*>(peers + part * BM + row) =
+        (static_cast<unsigned long long>(static_cast<uint32_t>(cur_s)) << 32) | __float_as_uint(ts[7]);
   }
   __device__ void end(bool ok) {
     if (ok && cur_s >= 0) flush(cur_s);
@@ -163,7 +214,9 @@ int tc_pieces() { return kPieces; }
 void tc_fill_sched(Ws& ws, int sm_count) {
   ws.tc_grid = sm_count;
   ws.tc_tn = (ws.N + BN - 1) / BN;
-  ws.tc_cmin = (ws.tc_tn + (kPieces - 2) - 1) / (kPieces - 2);
+  // a tile of Tn units meets at most ceil(Tn / cmin) + 1 CTA ranges of >= cmin units
+  constexpr int kMaxPieces = kPieces / EPI_PARTS;
+  ws.tc_cmin = (ws.tc_tn + (kMaxPieces - 2) - 1) / (kMaxPieces - 2);
 }
 
 cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {

@@ -55,9 +55,9 @@ struct EpiAct {
   __nv_bfloat16* out;
   __nv_bfloat16* outT;
   int row;
-  __device__ void begin(int, int, int, int row_) { row = row_; }
+  __device__ void begin(int, int, int, int row_, int, float*, unsigned long long*) { row = row_; }
   __device__ void unit(int, int) {}
-  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32], float*) {
+  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32]) {
     const int r = s * BM + row;
     const int cb = t * BN + c0;
     const bool rok = r < rows;
@@ -96,14 +96,14 @@ struct EpiF32 {
   const float* beta;
   float* out;
   int row;
-  __device__ void begin(int, int, int, int row_) { row = row_; }
+  __device__ void begin(int, int, int, int row_, int, float*, unsigned long long*) { row = row_; }
   __device__ void unit(int, int) {}
   __device__ float val(const uint32_t (&v)[32], int j, int r, int c, float bt) const {
     float o = __uint_as_float(v[j]) + (bias ? __ldg(bias + c) : 0.f);
     if (skipX) o = fmaf(bt, fabsf(__bfloat162float(skipX[static_cast<size_t>(r) * cols + c])), o);
     return o;
   }
-  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32], float*) {
+  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32]) {
     const int r = s * BM + row;
     if (r >= rows) return;
     const int cb = t * BN + c0;
@@ -144,13 +144,13 @@ struct EpiBCE {
   float* loss;
   int row;
   float lsum, bsum;
-  __device__ void begin(int, int, int, int row_) {
+  __device__ void begin(int, int, int, int row_, int, float*, unsigned long long*) {
     row = row_;
     lsum = 0.f;
     bsum = 0.f;
   }
   __device__ void unit(int, int) {}
-  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32], float*) {
+  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32]) {
     const int r = s * BM + row;
     const bool rok = r < rows;
     const int cb = t * BN + c0;
@@ -202,9 +202,9 @@ struct EpiGeluBwd {
   const float* Z1;
   __nv_bfloat16* dZT;
   int row;
-  __device__ void begin(int, int, int, int row_) { row = row_; }
+  __device__ void begin(int, int, int, int row_, int, float*, unsigned long long*) { row = row_; }
   __device__ void unit(int, int) {}
-  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32], float*) {
+  __device__ void chunk(int s, int t, int c0, const uint32_t (&v)[32]) {
     const int r = s * BM + row;
     if (r >= rows) return;
     const int cb = t * BN + c0;

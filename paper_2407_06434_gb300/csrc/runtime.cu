@@ -256,7 +256,9 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ws.Bpad = (ws.Bmax + kSigTile - 1) / kSigTile * kSigTile;
   ws.prec = d.precision;
   ws.topk = d.precision == OMP_PREC_FP32 ? 1 : h->d.rescore_topk;
-  ws.Fstride = static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2;
+  // padded to 4 entries so each signal's FP32 factor starts on a 16-byte boundary
+  ws.Fstride = (static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2 + 3) / 4 * 4;
+  ws.upd_w = update_default_warps(ws.Mp);
   ws.pieces = d.precision == OMP_PREC_FP32 ? 0 : tc_pieces();
   if (d.precision != OMP_PREC_FP32) tc_fill_sched(ws, h->sm_count);
   const size_t N = ws.N, Mp = ws.Mp, Bm = ws.Bmax, Bp = ws.Bpad, Sm = ws.Smax;
@@ -447,6 +449,84 @@ omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_
 }  // namespace
 
 extern "C" {
+
+omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
+                        int32_t repeats, int32_t* choice_out, void* stream) {
+  if (!h || !A || !Y || B < 1 || B > h->d.max_batch || S < 1 || S > h->d.max_iters || repeats < 1)
+    return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const char* cache = std::getenv("OMP_AUTOTUNE_CACHE");
+  char key[256];
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->dev) != cudaSuccess) return OMP_ERR_CUDA;
+  std::snprintf(key, sizeof(key), "%s M=%d N=%d prec=%d B=%lld S=%d", prop.name, h->ws.M, h->ws.N,
+                h->ws.prec, static_cast<long long>(B), S);
+  int best = 0;
+  if (cache) {  // a previous run's choice for the same key
+    if (FILE* f = std::fopen(cache, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof(line), f)) {
+        int w = 0;
+        char* bar = std::strrchr(line, '|');
+        if (bar && std::strncmp(line, key, std::strlen(key)) == 0 && line[std::strlen(key)] == '|' &&
+            std::sscanf(bar + 1, "%d", &w) == 1 && update_slots(h->ws.Mp, w))
+          best = w;
+      }
+      std::fclose(f);
+    }
+  }
+  if (!best) {
+    omp_status st = OMP_OK;
+    if (A != h->prepared_A) st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+    float* X = h->x_stage;
+    int* sup = h->s_stage;
+    CallArgs a{};
+    a.Y = Y;
+    a.X = X;
+    a.support = sup;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OMP_ERR_CUDA;
+    float best_ms = 0.f;
+    const int saved = h->ws.upd_w;
+    for (int w = 1; w <= 8; w <<= 1) {
+      if (!update_slots(h->ws.Mp, w)) continue;
+      h->ws.upd_w = w;
+      launch_set_args(h->args_dev, a, s);
+      enqueue_solve(h, static_cast<int>(B), S, eps, false, s);  // warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < repeats; ++r) enqueue_solve(h, static_cast<int>(B), S, eps, false, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        h->ws.upd_w = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return OMP_ERR_CUDA;
+      }
+      if (!best || ms < best_ms) {
+        best = w;
+        best_ms = ms;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cache) {
+      if (FILE* f = std::fopen(cache, "a")) {
+        std::fprintf(f, "%s|%d\n", key, best);
+        std::fclose(f);
+      }
+    }
+  }
+  if (best != h->ws.upd_w) {  // captured graphs hold the old launch shape
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+  }
+  h->ws.upd_w = best;
+  if (choice_out) *choice_out = best;
+  return check_launch();
+}
 
 omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out) {
   if (!h) return OMP_ERR_INVALID_ARGUMENT;

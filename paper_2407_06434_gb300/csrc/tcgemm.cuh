@@ -8,17 +8,24 @@
 // Schedule: units u = s * Tn + t over row tiles s and column tiles t; CTA g of Geff owns the
 // contiguous range [floor(g T / Geff), floor((g + 1) T / Geff)), Geff = min(grid, T / cmin).
 //
-// Roles (192 threads, one CTA per SM):
+// Roles (64 + 128 EPI_PARTS threads, one CTA per SM):
 //   warp 0 lane 0  TMA producer, 4 stages of 16 KB (A_op) + 32 KB (B_op)
 //   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
-//   warps 2..5     epilogue: tcgen05.ld of 32 columns (the next one in flight), functor call
+//   warps 2..      epilogue, EPI_PARTS warps per TMEM lane quarter (a warp may only read the
+//                  quarter warp % 4), each over EPI_COLS of the unit's 256 columns: tcgen05.ld
+//                  of 32 columns, functor call
 // Every mbarrier wait is bounded (about 2 s); a timeout raises OMP_DEVERR_WAIT_TIMEOUT, the
 // roles drain their own copies and MMAs, TMEM is freed and the CTA returns.
 //
-// Epilogue functor interface (one object per epilogue thread, `row` = its TMEM lane 0..127):
-//   void begin(int g, int T, int Geff, int row);
+// Epilogue functor interface (one object per epilogue thread, `row` = its TMEM lane 0..127,
+// `part` = which EPI_COLS of the unit's 256 columns it sees, starting at part * EPI_COLS):
+//   void begin(int g, int T, int Geff, int row, int part, float* scratch,
+//              unsigned long long* peers);
 //   void unit(int s, int t);                              // before the unit's chunks
-//   void chunk(int s, int t, int c0, const uint32_t (&v)[32], float* stage_row);
+// `scratch` is EPI_SCRATCH floats of shared memory private to the thread's warp; `peers` is
+// EPI_PARTS x BM 8-byte shared slots, [part][row], through which the threads of a row may
+// talk. The mainloop sets every slot to 0xffffffff00000000 before the first unit.
+//   void chunk(int s, int t, int c0, const uint32_t (&v)[32]);   // columns c0..c0+31 of the tile
 //   void end(bool ok);                                    // after the last unit
 #pragma once
 #include <cuda.h>
@@ -36,11 +43,16 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * KB;
 constexpr int B_BYTES = BN * KB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 192;
+constexpr int EPI_PARTS = kTcParts;           // epilogue warps per TMEM lane quarter
+constexpr int EPI_WARPS = 4 * EPI_PARTS;
+constexpr int EPI_COLS = BN / EPI_PARTS;      // columns of a unit each epilogue warp sees
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+static_assert(THREADS >= EPI_PARTS * BM, "the peer slots are initialised one per thread");
+static_assert(EPI_COLS % 32 == 0, "epilogue chunks are 32 columns");
 constexpr int TMEM_COLS = 2 * BN;
-constexpr int STAGE_ROW = 36;  // floats per staged score row (float4 stores without conflicts)
-constexpr int EPI_STAGE_BYTES = 4 * 32 * STAGE_ROW * 4;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + EPI_STAGE_BYTES;
+constexpr int EPI_SCRATCH = EPI_COLS;  // shared floats per epilogue warp
+constexpr int SMEM_BYTES =
+    STAGES * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_SCRATCH * 4 + EPI_PARTS * BM * 8;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -156,6 +168,20 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// v[j] for a run-time j without local memory: a 5-level select tree
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], int j) {
+  uint32_t a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = (j & 8) ? a[i + 8] : a[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = (j & 4) ? a[i + 4] : a[i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a[i] = (j & 2) ? a[i + 2] : a[i];
+  return (j & 1) ? a[1] : a[0];
+}
+
 // Insert (v, n) into a descending top-8; the caller has checked v > s[7]. Equal scores keep
 // the earlier (lower-index) entry in front.
 __device__ __forceinline__ void top8_insert(float (&s)[8], int (&ix)[8], float v, int n) {
@@ -212,13 +238,16 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull(a), 1);
-      mbar_init(tempty(a), 4);
+      mbar_init(tempty(a), EPI_WARPS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  unsigned long long* peers =
+      reinterpret_cast<unsigned long long*>(bars_gen + 256 + EPI_WARPS * EPI_SCRATCH * 4);
+  if (threadIdx.x < EPI_PARTS * BM) peers[threadIdx.x] = 0xffffffff00000000ull;  // tag -1
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(const_cast<uint32_t*>(tmem_slot))),
@@ -251,7 +280,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         mbar_expect_tx(full(stage), STAGE_BYTES);
         tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
         tma_load_2d(dst + A_BYTES, tm_b, kc * kelems, t * BN, full(stage));
-        last_ph[stage] = static_cast<int>(ph);
+#pragma unroll
+        for (int q = 0; q < STAGES; ++q)  // static indices keep last_ph in registers
+          if (q == stage) last_ph[q] = static_cast<int>(ph);
         if (++stage == STAGES) {
           stage = 0;
           ph ^= 1u;
@@ -308,8 +339,10 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     // ------------------------------------------------------------------ epilogue
     const int lg = warp & 3;           // TMEM lane quarter this warp may access
     const int row = lg * 32 + lane;    // row within the tile
-    float* stage_row = reinterpret_cast<float*>(bars_gen + 256) + ((warp - 2) * 32 + lane) * STAGE_ROW;
-    epi.begin(g, T, Geff, row);
+    const int part = (warp - 2) / 4;   // which EPI_COLS of the unit's columns
+    constexpr int CH = EPI_COLS / 32;  // 32-column chunks per part
+    float* scratch = reinterpret_cast<float*>(bars_gen + 256) + (warp - 2) * EPI_SCRATCH;
+    epi.begin(g, T, Geff, row, part, scratch, peers);
     int acc = 0;
     uint32_t aph = 0;
     bool ok = true;
@@ -321,21 +354,22 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) + static_cast<uint32_t>(acc * BN);
-      uint32_t va[32], vb[32];
-      tmem_ld32_issue(taddr, va);
-      tmem_ld_wait();
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) +
+                             static_cast<uint32_t>(acc * BN + part * EPI_COLS);
+      // one 32-column load at a time; once the last load has landed the accumulator goes back
+      // to the MMA before that chunk is scanned
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t (&cur)[32] = (c & 1) ? vb : va;
-        uint32_t (&nxt)[32] = (c & 1) ? va : vb;
-        if (c + 1 < BN / 32) tmem_ld32_issue(taddr + (c + 1) * 32, nxt);
-        epi.chunk(s, t, c * 32, cur, stage_row);
-        if (c + 1 < BN / 32) tmem_ld_wait();
+      for (int c = 0; c < CH; ++c) {
+        uint32_t cur[32];
+        tmem_ld32_issue(taddr + c * 32, cur);
+        tmem_ld_wait();
+        if (c + 1 == CH) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty(acc));
+        }
+        epi.chunk(s, t, part * EPI_COLS + c * 32, cur);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty(acc));
       acc ^= 1;
       if (acc == 0) aph ^= 1u;
     }

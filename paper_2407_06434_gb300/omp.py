@@ -36,7 +36,7 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_gradients", "omp_proposal_infer", "omp_proposal_set_thresholds",
            "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
-           "omp_synthesize_signals", "omp_solve_batch_learned"]
+           "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -108,6 +108,7 @@ def load(path: Optional[str] = None):
                                               _P, _P, _P]),
         "omp_synthesize_signals": (_I32, [_P, _I64, _I64, _P, _P, _P, _I64, _I32, _P, _P]),
         "omp_solve_batch_learned": (_I32, [_P, _P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
+        "omp_autotune": (_I32, [_P, _P, _P, _I64, _I32, _F32, _I32, ctypes.POINTER(_I32), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +274,15 @@ def omp_solve_batch_trace(h: Handle, A, Y, S: int, eps: float, X_out, support_ou
     _check(load().omp_solve_batch_trace(h.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps, _ptr(X_out),
                                         _ptr(support_out), _ptr(drop_out), _stream(stream)),
            "omp_solve_batch_trace")
+
+
+def omp_autotune(h: Handle, A, Y, S: int, eps: float = 0.0, repeats: int = 2, stream=None) -> int:
+    """Pick the fastest append/update launch shape for this workload; returns warps per signal."""
+    _check_A(A, h.M, h.N)
+    c = _I32(0)
+    _check(load().omp_autotune(h.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps, repeats,
+                               ctypes.byref(c), _stream(stream)), "omp_autotune")
+    return c.value
 
 
 def omp_handle_info(h: Handle):

@@ -262,3 +262,33 @@ def test_correlate_top8_quantised(prec):
             np.testing.assert_allclose(np.sort(sc[b])[::-1], S[b, order[:8]], rtol=2e-5)
             checked += 1
     assert checked > 0.9 * B
+
+
+def test_autotune_choice_and_cache(tmp_path, monkeypatch):
+    """The autotuner picks a valid update-kernel shape (warps per signal), results still match
+    the oracle after the switch, and a second handle reads the recorded choice from the cache
+    file instead of timing again."""
+    from paper_2407_06434_gb300 import omp
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("OMP_AUTOTUNE_CACHE", str(cache))
+    w = gen.get_config("gaussian_64x256_s8_b16", M=1024, N=2048, B=512, S=16, s_min=16, s_max=16,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=13)
+    Y, *_ = gen.signals(w, A, seed=13)
+    Ad, Yd = dev_dict(A), torch.from_numpy(Y).cuda()
+    s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+    X, S_ = s.solve(Ad, Yd, w.S)                     # captures a graph with the default shape
+    choice = omp.omp_autotune(s.h, Ad, Yd, w.S, 0.0, repeats=1)
+    assert choice in (1, 2, 4, 8)
+    X, S_, n_iter, resid, stop = s.solve(Ad, Yd, w.S, diagnostics=True)
+    torch.cuda.synchronize()
+    rows = np.arange(0, w.B, 16)
+    ref = oracle.omp_batch(A, Y[rows], w.S)
+    parity.compare(A, Y[rows], ref, S_.cpu().numpy()[rows], X.cpu().numpy()[rows],
+                   n_iter.cpu().numpy()[rows], resid.cpu().numpy()[rows], rows=rows)
+    s.close()
+    assert cache.read_text().strip().endswith(f"|{choice}")
+    s2 = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+    assert omp.omp_autotune(s2.h, Ad, Yd, w.S, 0.0, repeats=1) == choice
+    assert len(cache.read_text().strip().splitlines()) == 1
+    s2.close()

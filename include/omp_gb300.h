@@ -66,7 +66,10 @@ typedef struct omp_desc {
   int32_t precision;     /* omp_precision */
   int32_t rescore_topk;  /* quantised paths: candidates rescored in FP32, 1..8 (0 means 8) */
   int32_t eps_relative;  /* 1: stop when ||r_k|| <= eps * ||y||; 0: when ||r_k|| <= eps (Alg. 1) */
-  int32_t use_graph;     /* 1: capture each (B, S, eps) solve once as a CUDA graph and replay it */
+  int32_t use_graph;     /* capture each (B, S, eps) solve once as a CUDA graph and replay it:
+                            1 with the S iterations unrolled (kernels of an iteration with no live
+                            signal return at once), 2 with the iterations as a device-side while
+                            loop that ends when no signal is live; 0: direct launches */
   int32_t device;        /* CUDA device ordinal the handle lives on */
 } omp_desc;
 
@@ -185,6 +188,13 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
 
 /* The descriptor the handle was created with (after defaults) and the device's SM count. */
 omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out);
+
+/* Passes of the device-side iteration loop in the last solve on `stream` (with use_graph = 2 the
+ * captured graph runs the iterations as a conditional while node that stops after S passes or
+ * as soon as no signal is live): the largest per-signal iteration count, at least 1; 0 when the
+ * last solve ran its iterations unrolled (use_graph 0 or 1, or profiling on). Synchronises
+ * `stream`. */
+omp_status omp_loop_passes(omp_handle h, int32_t* passes_out, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Learned proposal. A small network maps the first correlation of a signal,

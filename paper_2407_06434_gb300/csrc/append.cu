@@ -149,6 +149,7 @@ __device__ __forceinline__ void append_column(const Ws& ws, const GroupSmem& gs,
 template <int W, int V>
 __global__ void __launch_bounds__(kThreads, 2)
     append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
+  k = iter_of(ws, k);
   const bool top1 = ws.prec == OMP_PREC_FP32;
   constexpr int GPB = 8 / W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

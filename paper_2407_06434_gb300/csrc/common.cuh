@@ -65,6 +65,7 @@ struct Ws {
   float* sr[2];
   int* live[2];
   int* cnt;
+  int* kdev;       // iteration counter of the graph's device-side loop
   uint8_t* flag;
   unsigned long long* cand1;
   float* cand_s;
@@ -148,6 +149,11 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return out;
 }
 
+// Iteration index of a per-iteration kernel: the launch's own k, or, when the launch passes -1
+// (the body of the graph's device-side while loop, identical for every iteration), the counter
+// that the loop advances.
+__device__ __forceinline__ int iter_of(const Ws& ws, int k) { return k >= 0 ? k : *ws.kdev; }
+
 // Persistent schedule of the tensor-core correlation (shared by the correlation kernel, which
 // writes candidate slots, and the kernels that merge them). Units u = s * Tn + t over signal
 // tiles s and atom tiles t; Geff CTAs each own a contiguous range of at least `cmin` units.
@@ -181,7 +187,8 @@ void launch_gram_simt(const Ws& ws, cudaStream_t s);
 void launch_corr_simt(const Ws& ws, int k, int B, cudaStream_t s);
 void launch_init(const Ws& ws, const CallArgs* args, int B, cudaStream_t s);
 void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s);
-void launch_compact(const Ws& ws, int j, int B, cudaStream_t s);
+void launch_compact(const Ws& ws, int j, int B, int S, cudaStream_t s);
+void launch_advance(const Ws& ws, int S, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
 void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStream_t s);
 void launch_topk_out(const Ws& ws, const CallArgs* args, int B, int topk, cudaStream_t s);

@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
   if (GRAM) {
     L = ws.N;
   } else {
+    k = iter_of(ws, k);
     L = ws.cnt[k + 1];
     live = ws.live[k & 1];
   }

@@ -191,6 +191,7 @@ template <int PREC>
 __global__ void __launch_bounds__(THREADS, 1)
     corr_tc_kernel(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
                    const __grid_constant__ CUtensorMap tm_a, Ws ws, int k) {
+  k = iter_of(ws, k);
   const int L = ws.cnt[k + 1];
   if (L <= 0) return;
   EpiTop8 epi;

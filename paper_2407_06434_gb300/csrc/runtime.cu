@@ -33,6 +33,7 @@ struct omp_handle_s {
   const float* prepared_A = nullptr;
   CallArgs* args_dev = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t body_stream = nullptr;  // captures the body of the graph's while loop
   std::vector<GraphEntry> graphs;
   std::vector<void*> allocs;
   float* y_stage = nullptr;
@@ -94,6 +95,8 @@ void release(omp_handle_s* h) {
   h->allocs.clear();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
+  if (h->body_stream) cudaStreamDestroy(h->body_stream);
+  h->body_stream = nullptr;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -119,7 +122,7 @@ void prof_mark(omp_handle_s* h, bool prof, int kind, int k, int end, cudaStream_
 void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStream_t s) {
   const Ws& ws = h->ws;
   launch_init(ws, h->args_dev, B, s);
-  launch_compact(ws, 0, B, s);
+  launch_compact(ws, 0, B, S, s);
   for (int k = 0; k < S; ++k) {
     prof_mark(h, prof, 0, k, 0, s);
     enqueue_correlate(h, k, B, s);
@@ -127,14 +130,68 @@ void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStre
     prof_mark(h, prof, 1, k, 0, s);
     launch_update(ws, k, B, S, eps, h->d.eps_relative, s);
     prof_mark(h, prof, 1, k, 1, s);
-    if (k + 1 < S) launch_compact(ws, k + 1, B, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, B, S, s);
   }
   launch_finalize(ws, h->args_dev, B, S, s);
 }
 
+// The same solve as one graph whose iterations are a device-side while loop (a conditional
+// node): the body (correlate, update, compact, advance) reads the iteration from the counter
+// that the init kernel zeroes, and the advance kernel ends the loop after S iterations or as
+// soon as no signal is live, so a batch that converges early launches no further kernels.
+bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* out) {
+  const Ws& ws = h->ws;
+  cudaStream_t s = h->cap_stream;
+  *out = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  launch_init(ws, h->args_dev, B, s);
+  launch_compact(ws, 0, B, S, s);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  bool ok = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd) == cudaSuccess &&
+            st == cudaStreamCaptureStatusActive;
+  cudaGraphConditionalHandle cond{};
+  cudaGraphNode_t node = nullptr;
+  cudaGraph_t body = nullptr;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np) == cudaSuccess;
+    if (ok) body = np.conditional.phGraph_out[0];
+  }
+  if (ok)
+    ok = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    enqueue_correlate(h, -1, B, h->body_stream);
+    launch_update(ws, -1, B, S, eps, h->d.eps_relative, h->body_stream);
+    launch_compact(ws, -1, B, S, h->body_stream);
+    launch_advance(ws, S, cond, h->body_stream);
+    cudaGraph_t tmp = nullptr;
+    ok = cudaStreamEndCapture(h->body_stream, &tmp) == cudaSuccess;
+  }
+  if (ok) ok = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) == cudaSuccess;
+  if (ok) launch_finalize(ws, h->args_dev, B, S, s);
+  cudaGraph_t graph = nullptr;
+  const bool ended = cudaStreamEndCapture(s, &graph) == cudaSuccess && graph != nullptr;
+  if (!ok || !ended) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return false;
+  }
+  *out = graph;
+  return true;
+}
+
 void enqueue_topk(omp_handle_s* h, const float* R, int B, int topk, cudaStream_t s) {
   launch_load_rows(h->ws, R, B, s);
-  launch_compact(h->ws, 0, B, s);
+  launch_compact(h->ws, 0, B, 1, s);
   enqueue_correlate(h, 0, B, s);
   launch_topk_out(h->ws, h->args_dev, B, topk, s);
 }
@@ -160,12 +217,27 @@ omp_status run_solve(omp_handle_s* h, int B, int S, float eps, cudaStream_t stre
       return cudaGraphLaunch(g.exec, stream) == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
   // capture on the handle's own stream (capture only records; the replay below runs in the
   // caller's stream order)
+  // The unrolled form is the default: on GB300 each pass of a conditional while node costs about
+  // 5.5 us more than an unrolled iteration, which is about what three launches that return at
+  // once cost, so the loop saves nothing even when a batch converges early. The profiled form
+  // is always unrolled, with an event pair around each kernel.
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  if (ok) {
-    enqueue_solve(h, B, S, eps, prof, h->cap_stream);
-    ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
+  bool ok = false;
+  if (prof) {
+    ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enqueue_solve(h, B, S, eps, prof, h->cap_stream);
+      ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
+    }
+  } else if (h->d.use_graph == 2) {
+    ok = capture_while_solve(h, B, S, eps, &graph);
+  } else {
+    ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enqueue_solve(h, B, S, eps, false, h->cap_stream);
+      ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
+    }
   }
   if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
   if (graph) cudaGraphDestroy(graph);
@@ -227,7 +299,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   if (d.M < 1 || d.M > 8192 || d.N < 2 || d.N > 65536 || d.max_batch < 1 ||
       d.max_batch > (1 << 24) || d.max_iters < 1 || d.max_iters > 256 || d.max_iters > d.M ||
       d.max_iters > d.N || d.precision < 0 || d.precision > 2 || d.rescore_topk < 0 ||
-      d.rescore_topk > kMaxTopk)
+      d.rescore_topk > kMaxTopk || d.use_graph < 0 || d.use_graph > 2)
     return OMP_ERR_INVALID_ARGUMENT;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || d.device < 0 || d.device >= ndev) {
@@ -282,7 +354,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
          dalloc(h, &ws.cand_i, Bp * ws.pieces * kMaxTopk);
   }
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
-  ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
+  ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
        dalloc(h, &ws.F32, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
        dalloc(h, &ws.sup, Bm * Sm);
@@ -300,6 +372,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
                  (!ws.escale || cudaMemset(ws.escale, 0, Npad * sizeof(float)) == cudaSuccess) &&
                  cudaMemset(ws.cand1, 0, Bm * sizeof(unsigned long long)) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  configure_update_kernels(ws) == cudaSuccess;
   if (cuda_ok && d.precision != OMP_PREC_FP32) cuda_ok = tc_setup(ws, h->sm_count, &h->tc) == cudaSuccess;
   if (cuda_ok) cuda_ok = cudaDeviceSynchronize() == cudaSuccess;
@@ -437,11 +510,11 @@ omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_
   if (!launch_restricted(ws, h->args_dev, cand, K, tau, b, S, eps, h->d.eps_relative, ws.fb, s))
     return OMP_ERR_CUDA;
   // signals that failed the residual-drop check continue in the dense loop
-  launch_compact(ws, 0, b, s);
+  launch_compact(ws, 0, b, S, s);
   for (int k = 0; k < S; ++k) {
     enqueue_correlate(h, k, b, s);
     launch_update(ws, k, b, S, eps, h->d.eps_relative, s);
-    if (k + 1 < S) launch_compact(ws, k + 1, b, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, b, S, s);
   }
   launch_finalize(ws, h->args_dev, b, S, s);
   return check_launch();
@@ -532,6 +605,18 @@ omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_o
   if (!h) return OMP_ERR_INVALID_ARGUMENT;
   if (desc_out) *desc_out = h->d;
   if (sm_count_out) *sm_count_out = h->sm_count;
+  return OMP_OK;
+}
+
+omp_status omp_loop_passes(omp_handle h, int32_t* passes_out, void* stream) {
+  if (!h || !passes_out) return OMP_ERR_INVALID_ARGUMENT;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, h->ws.kdev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return OMP_ERR_CUDA;
+  *passes_out = v;
   return OMP_OK;
 }
 

@@ -19,6 +19,7 @@ void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s) {
 __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, int B) {
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ws.kdev = 0;
   if (b >= B) return;
   const float* y = args->Y + static_cast<size_t>(b) * ws.M;
   float* r = ws.R32 + static_cast<size_t>(b) * ws.Mp;
@@ -79,7 +80,9 @@ void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s) {
 // tensor-core paths, their residual row quantised into position order (Rq[j&1], sr[j&1]).
 constexpr int kCompactChunk = 64;
 
-__global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j) {
+__global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
+  j = j >= 0 ? j : *ws.kdev + 1;  // -1: the step after the loop's current iteration
+  if (j >= S) return;           // no further iteration reads this list
   __shared__ int dest_s[kCompactChunk];
   __shared__ int red_i[8];
   __shared__ int half_s[2];
@@ -156,8 +159,21 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j) {
   }
 }
 
-void launch_compact(const Ws& ws, int j, int B, cudaStream_t s) {
-  compact_kernel<<<(B + kCompactChunk - 1) / kCompactChunk, 256, 0, s>>>(ws, j);
+void launch_compact(const Ws& ws, int j, int B, int S, cudaStream_t s) {
+  compact_kernel<<<(B + kCompactChunk - 1) / kCompactChunk, 256, 0, s>>>(ws, j, S);
+}
+
+// End of one pass of the graph's while loop: advance the iteration counter and keep looping
+// while iterations remain and some signal is live for the next one (its count was just written
+// by the compaction).
+__global__ void advance_kernel(Ws ws, int S, cudaGraphConditionalHandle cond) {
+  const int k1 = *ws.kdev + 1;
+  *ws.kdev = k1;
+  cudaGraphSetConditional(cond, (k1 < S && ws.cnt[k1 + 1] > 0) ? 1u : 0u);
+}
+
+void launch_advance(const Ws& ws, int S, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  advance_kernel<<<1, 1, 0, s>>>(ws, S, cond);
 }
 
 // ---------------------------------------------------------------------------------- finalize

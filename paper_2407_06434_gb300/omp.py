@@ -36,7 +36,8 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_gradients", "omp_proposal_infer", "omp_proposal_set_thresholds",
            "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
-           "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune"]
+           "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
+           "omp_loop_passes"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -91,6 +92,7 @@ def load(path: Optional[str] = None):
         "omp_correlate_argmax_noalloc": (_I32, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
         "omp_solve_batch_trace": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P]),
         "omp_handle_info": (_I32, [_P, ctypes.POINTER(omp_desc), ctypes.POINTER(_I32)]),
+        "omp_loop_passes": (_I32, [_P, ctypes.POINTER(_I32), _P]),
         "omp_proposal_desc_default": (None, [ctypes.POINTER(omp_proposal_desc)]),
         "omp_proposal_create": (_I32, [_P, ctypes.POINTER(omp_proposal_desc), ctypes.POINTER(_P)]),
         "omp_proposal_destroy": (_I32, [_P]),
@@ -172,7 +174,7 @@ class Handle:
 
 def omp_create(M: int, N: int, max_batch: int = 4096, max_iters: int = 64,
                precision: str = "bf16", rescore_topk: int = 8, eps_relative: bool = True,
-               use_graph: bool = True, device: int = 0) -> Handle:
+               use_graph: int = 1, device: int = 0) -> Handle:
     lib = load()
     d = omp_desc()
     lib.omp_desc_default(ctypes.byref(d), M, N)
@@ -290,6 +292,13 @@ def omp_handle_info(h: Handle):
     sms = _I32(0)
     _check(load().omp_handle_info(h.ptr, ctypes.byref(d), ctypes.byref(sms)), "omp_handle_info")
     return d, sms.value
+
+
+def omp_loop_passes(h: Handle, stream=None) -> int:
+    """Passes of the device-side iteration loop in the last graph solve (0 if it ran unrolled)."""
+    v = _I32(0)
+    _check(load().omp_loop_passes(h.ptr, ctypes.byref(v), _stream(stream)), "omp_loop_passes")
+    return v.value
 
 
 def omp_synthesize_signals(A, sup, coef, noise, Y_out, stream=None):

@@ -154,6 +154,43 @@ def test_graph_replay_and_direct_launches_agree(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_device_loop_stops_when_no_signal_is_live(prec):
+    """With use_graph = 2 the graph runs the iterations as a device-side while loop: with a
+    relative eps that every signal reaches after about s iterations it stops after max(n_iter)
+    passes, well before S, and gives bit-identical results to direct launches and to the unrolled
+    graph; an all-zero batch takes one pass."""
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", M=128, N=512, B=100, S=32, s_min=2, s_max=6,
+                       sigma=1e-6, col_scale=1.0)
+    A = gen.dictionary(w, seed=8)
+    Y, *_ = gen.signals(w, A, seed=8)
+    Ad = dev_dict(A)
+    Yd = torch.from_numpy(Y).cuda()
+    res = {}
+    for use_graph in (2, 1, 0):
+        s = omp.OmpSolver(w.M, w.N, max_batch=128, max_iters=w.S, precision=prec,
+                          use_graph=use_graph)
+        for _ in range(2):
+            X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, 1e-3, diagnostics=True)
+        torch.cuda.synchronize()
+        res[use_graph] = (X.cpu().numpy(), sup.cpu().numpy(), n_iter.cpu().numpy(),
+                          omp.omp_loop_passes(s.h))
+        if use_graph == 2:
+            Z = torch.zeros_like(Yd)
+            s.solve(Ad, Z, w.S, 1e-3)
+            assert omp.omp_loop_passes(s.h) == 1
+            assert np.array_equal(s.solve(Ad, Z, w.S, 1e-3)[1].cpu().numpy(), np.full((w.B, w.S), -1))
+        s.close()
+    Xg, supg, ng, passes = res[2]
+    for other in (1, 0):
+        Xd, supd, nd, passes_other = res[other]
+        assert passes_other == 0
+        assert np.array_equal(supg, supd) and np.array_equal(ng, nd)
+        assert np.array_equal(Xg.view(np.uint32), Xd.view(np.uint32))
+    assert passes == int(ng.max()) and passes < w.S
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_host_entry_point(prec):
     from paper_2407_06434_gb300 import omp
     w = gen.get_config("gaussian_64x256_s8_b16", B=64)

@@ -22,7 +22,10 @@
 namespace ompk {
 namespace {
 
-constexpr int kThreads = 256;
+// One block per signal (W warps): a block's slot on the SM frees as soon as its own signal is
+// done, so signals that skip the rescoring or retire early are not held back by slower ones of
+// the same block. W * 32 threads x (16 / W) blocks keep 128 registers a thread and 16 warps per
+// SM.
 constexpr int kMaxBlk = 8;  // lane slots of 32 rows/columns of F: Smax <= 256
 constexpr int kTriMax = 64;  // the packed FP32 factor is staged in shared memory for Smax <= 64
 
@@ -47,7 +50,8 @@ struct GroupSmem {
   float* cpart;  // 8 x 8: rescoring partial dot products [candidate][warp]
   int* cidx;     // 8
   double* part;  // 16: per-warp partials of b and ||r||^2
-  int* scal;     // 4: n*, dependent flag
+  int* scal;     // 4: n*, dependent flag, rescoring skipped
+  float* top2;   // 2: the merged lists' best and second-best quantised scores
   float* tri;    // Smax (Smax + 1) / 2 when Smax <= kTriMax: staged copy of the packed FP32 F
 };
 
@@ -57,7 +61,7 @@ __host__ __device__ __forceinline__ size_t tri_floats(int Smax) {
 
 __host__ __device__ __forceinline__ size_t group_bytes(int Smax) {
   const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
-                   8 * 4 + 16 * 8 + 16 + (tri_floats(Smax) * 4 + 15) / 16 * 16;
+                   8 * 4 + 16 * 8 + 16 + 8 + (tri_floats(Smax) * 4 + 15) / 16 * 16;
   return (b + 15) / 16 * 16;
 }
 
@@ -74,6 +78,7 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, in
   s.scal = s.cidx + 8;
   s.w = reinterpret_cast<float*>(s.scal + 4);
   s.z = s.w + Smax;
+  s.top2 = s.z + Smax;
   return s;
 }
 
@@ -147,22 +152,38 @@ __device__ __forceinline__ void append_column(const Ws& ws, const GroupSmem& gs,
 }
 
 template <int W, int V>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(W * 32, 16 / W)
     append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
   k = iter_of(ws, k);
   const bool top1 = ws.prec == OMP_PREC_FP32;
-  constexpr int GPB = 8 / W;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = warp / W, wig = warp - grp * W;
+  const int lane = threadIdx.x & 31;
+  const int grp = 0, wig = threadIdx.x >> 5;
   const int L = ws.cnt[k + 1];
-  const int p = blockIdx.x * GPB + grp;
+  const int p = blockIdx.x;
   if (p >= L) return;  // the whole group leaves together
   const int id = ws.live[k & 1][p];
   const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
   extern __shared__ __align__(16) unsigned char smem[];
   GroupSmem gs = group_smem(smem, grp, ws.Smax);
 
-  // Loads that do not depend on the selection go out first: the packed FP32 factor (staged in
+  // The candidate lists head the critical path (merge, rescoring, append), so their loads are
+  // issued first; they are only read at the merge below.
+  float vs[8];
+  int vi[8];
+  if (!top1 && wig == 0) {
+    const int total = tc_piece_count(ws, L, p) * kMaxTopk;
+    const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+    const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = lane + 32 * t;
+      const bool ok = e < total;
+      vs[t] = ok ? cs[e] : -1.f;
+      vi[t] = ok ? ci[e] : 0x7fffffff;
+    }
+  }
+
+  // Loads that do not depend on the selection go out next: the packed FP32 factor (staged in
   // shared memory with 16-byte loads, so the serial z and F z loops wait on no global load), the
   // support, and the norms used at the end.
   float* Ff = ws.F32 + static_cast<size_t>(id) * ws.Fstride;
@@ -196,22 +217,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     ns = key_index(ws.cand1[p]);
   } else {
     if (wig == 0) {
-      const int total = tc_piece_count(ws, L, p) * kMaxTopk;
-      const float* cs = ws.cand_s + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
-      const int* ci = ws.cand_i + static_cast<size_t>(p) * ws.pieces * kMaxTopk;
-      float vs[8];
-      int vi[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int e = lane + 32 * t;
-        const bool ok = e < total;
-        vs[t] = ok ? cs[e] : -1.f;
-        vi[t] = ok ? ci[e] : 0x7fffffff;
-        if (vi[t] < 0) {
+      for (int t = 0; t < 8; ++t)
+        if (vi[t] < 0) {  // an unfilled list entry
           vs[t] = -1.f;
           vi[t] = 0x7fffffff;
         }
-      }
       for (int sel = 0; sel < ws.topk; ++sel) {
         float bs = -2.f;
         int bi = 0x7fffffff, bt = -1;
@@ -242,12 +253,23 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
         if (lane == 0) gs.cidx[sel] = (g_i >= 0 && g_i < ws.N) ? g_i : -1;
+        if (lane == 0 && sel < 2) gs.top2[sel] = g_s;
+      }
+      // The rescoring can only confirm the quantised best when its lead over the second is
+      // more than twice the bound on |quantised - FP32| score (rescore_eps ||r||, from the
+      // quantisation and both accumulations, with ||a|| inv_norm = 1): every other candidate's
+      // FP32 score is then strictly below the best one's, so the rescoring is skipped.
+      if (lane == 0) {
+        const float lead = gs.top2[0] - gs.top2[1];
+        gs.scal[2] = (ws.rescore_eps > 0.f && rprev > 1e-30f && gs.cidx[0] >= 0 &&
+                      lead > 2.f * ws.rescore_eps * rprev) ? 1 : 0;
       }
     }
     group_sync(W, grp);
+    const bool skip = gs.scal[2] != 0;
     // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
     // candidates per pass so their row loads are in flight together
-    for (int c = 0; c < ws.topk; c += 2) {
+    for (int c = 0; !skip && c < ws.topk; c += 2) {
       const int n0 = gs.cidx[c];
       const int n1 = c + 1 < ws.topk ? gs.cidx[c + 1] : -1;
       const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n0 < 0 ? 0 : n0) * ws.Mp);
@@ -271,7 +293,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     group_sync(W, grp);
-    if (wig == 0) {
+    if (wig == 0 && skip) {
+      if (lane == 0) gs.scal[0] = gs.cidx[0];
+    } else if (wig == 0) {
       float sc = -2.f;
       int ix = 0x7fffffff;
       if (lane < ws.topk && gs.cidx[lane] >= 0) {
@@ -418,9 +442,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 // W warps per signal and V float4 slots per lane cover Mp <= 128 W V.
 template <int W, int V>
 void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  constexpr int GPB = 8 / W;
-  const size_t smem = group_bytes(ws.Smax) * GPB;
-  append_update_kernel<W, V><<<(B + GPB - 1) / GPB, kThreads, smem, s>>>(ws, k, S, eps, eps_rel);
+  const size_t smem = group_bytes(ws.Smax);
+  append_update_kernel<W, V><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
 }
 
 template <int W>
@@ -439,7 +462,7 @@ cudaError_t set_attr_t(int bytes) {
 
 template <int W>
 cudaError_t set_attr_w(const Ws& ws) {
-  const int bytes = static_cast<int>(group_bytes(ws.Smax) * (8 / W));
+  const int bytes = static_cast<int>(group_bytes(ws.Smax));
   cudaError_t e = set_attr_t<W, 1>(bytes);
   if (e == cudaSuccess) e = set_attr_t<W, 2>(bytes);
   if (e == cudaSuccess) e = set_attr_t<W, 4>(bytes);

@@ -66,6 +66,7 @@ struct Ws {
   int* live[2];
   int* cnt;
   int* kdev;       // iteration counter of the graph's device-side loop
+  float rescore_eps;  // bound on |quantised score - FP32 score| per unit of ||r|| (0: none)
   uint8_t* flag;
   unsigned long long* cand1;
   float* cand_s;

@@ -328,6 +328,21 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ws.Bpad = (ws.Bmax + kSigTile - 1) / kSigTile * kSigTile;
   ws.prec = d.precision;
   ws.topk = d.precision == OMP_PREC_FP32 ? 1 : h->d.rescore_topk;
+  // |BF16 score - FP32 score| <= rescore_eps ||r|| (||a|| inv_norm = 1): BF16 rounding of a and
+  // r (unit roundoff 2^-8) gives 2^-7 + 2^-16 of sum |a_m r_m| <= ||a|| ||r||; the tensor-core
+  // accumulation is allowed 2^-22 and the FP32 rescoring 2^-24 per addition over Mp terms; 1%
+  // covers the rounding of inv_norm and of the stored ||r||. E4M3 operands get no such bound
+  // (their subnormal range breaks the relative one), so FP8 always rescores.
+  // (test hook: OMP_RESCORE_ALWAYS=1 turns the shortcut off)
+  const char* always = std::getenv("OMP_RESCORE_ALWAYS");
+  if (ws.prec == OMP_PREC_BF16 && !(always && std::atoi(always) == 1)) {
+    const double u = std::ldexp(1.0, -8), m = static_cast<double>(ws.Mp);
+    const double g_tc = m * std::ldexp(1.0, -22) / (1.0 - m * std::ldexp(1.0, -22));
+    const double g_32 = m * std::ldexp(1.0, -24) / (1.0 - m * std::ldexp(1.0, -24));
+    ws.rescore_eps = static_cast<float>(1.01 * (2 * u + u * u + (1 + u) * (1 + u) * g_tc + g_32));
+  } else {
+    ws.rescore_eps = 0.f;
+  }
   // padded to 4 entries so each signal's FP32 factor starts on a 16-byte boundary
   ws.Fstride = (static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2 + 3) / 4 * 4;
   ws.upd_w = update_default_warps(ws.Mp);

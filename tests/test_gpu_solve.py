@@ -190,6 +190,30 @@ def test_device_loop_stops_when_no_signal_is_live(prec):
     assert passes == int(ng.max()) and passes < w.S
 
 
+def test_rescoring_shortcut_is_exact(monkeypatch):
+    """BF16 skips the FP32 rescoring when the quantised best leads the second by more than twice
+    the quantisation error bound; the supports and coefficients must be bit-identical to always
+    rescoring, on a workload with many close calls (coherent pairs, noise-level late steps)."""
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=2048, B=512, S=48, s_min=8, s_max=40,
+                       sigma=1e-2, col_scale=1.0)
+    A = gen.dictionary(w, seed=11)
+    Y, *_ = gen.signals(w, A, seed=11)
+    Ad = dev_dict(A)
+    Yd = torch.from_numpy(Y).cuda()
+    out = {}
+    for always in ("0", "1"):
+        monkeypatch.setenv("OMP_RESCORE_ALWAYS", always)
+        s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+        X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, 0.0, diagnostics=True)
+        torch.cuda.synchronize()
+        out[always] = (X.cpu().numpy(), sup.cpu().numpy(), resid.cpu().numpy())
+        s.close()
+    assert np.array_equal(out["0"][1], out["1"][1])
+    assert np.array_equal(out["0"][0].view(np.uint32), out["1"][0].view(np.uint32))
+    assert np.array_equal(out["0"][2].view(np.uint32), out["1"][2].view(np.uint32))
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_host_entry_point(prec):
     from paper_2407_06434_gb300 import omp

@@ -74,18 +74,18 @@ void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ compaction
 // Compaction step j: keeps the positions of list live[(j+1)&1] (count cnt[j]) whose flag is
-// set, in order, into live[j&1]; writes cnt[j+1]. Each block owns 64 positions and counts the
-// kept flags before its range itself (at most Bmax bytes), so the compaction is stable and
-// needs no inter-block communication. Kept signals get their candidate key cleared and, on the
-// tensor-core paths, their residual row quantised into position order (Rq[j&1], sr[j&1]).
-constexpr int kCompactChunk = 64;
+// set, in order, into live[j&1]; writes cnt[j+1]. Each block owns kCompactChunk positions and
+// counts the kept flags before its range itself (16 flags per load), so the compaction is
+// stable and needs no inter-block communication. Kept signals get their candidate key cleared
+// and, on the tensor-core paths, their residual row quantised into position order (Rq[j&1],
+// sr[j&1]); one warp per row, the row's loads issued together in batches of 8 per lane.
+constexpr int kCompactChunk = 16;
 
 __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
   j = j >= 0 ? j : *ws.kdev + 1;  // -1: the step after the loop's current iteration
   if (j >= S) return;           // no further iteration reads this list
   __shared__ int dest_s[kCompactChunk];
   __shared__ int red_i[8];
-  __shared__ int half_s[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Lin = ws.cnt[j];
   const int* in = ws.live[(j + 1) & 1];
@@ -95,65 +95,97 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
     if (blockIdx.x == 0 && tid == 0) ws.cnt[j + 1] = 0;
     return;
   }
-  // kept flags before p0
+  // kept flags before p0 (a multiple of 16; flags are 0 or 1 bytes, so a word's bit count is
+  // its number of kept positions)
   int c = 0;
-  const uint8_t* fl = ws.flag;
-  for (int i = tid; i < p0; i += 256) c += fl[i];
+  const uint4* fl4 = reinterpret_cast<const uint4*>(ws.flag);
+  for (int i = tid; i < p0 / 16; i += 256) {
+    const uint4 v = fl4[i];
+    c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+  }
   c = warp_sum_int(c);
   if (lane == 0) red_i[warp] = c;
+  if (warp == 0) {
+    const int p = p0 + lane;
+    const bool keep = lane < kCompactChunk && p < Lin && ws.flag[p] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane < kCompactChunk) dest_s[lane] = keep ? __popc(m & ((1u << lane) - 1u)) : -1;
+  }
   __syncthreads();
   int before = 0;
 #pragma unroll
   for (int w = 0; w < 8; ++w) before += red_i[w];
-  if (warp < 2) {
-    const int p = p0 + warp * 32 + lane;
-    const bool keep = p < Lin && fl[p] != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    const int rank = __popc(m & ((1u << lane) - 1u));
-    dest_s[warp * 32 + lane] = keep ? rank : -1;
-    if (lane == 0) half_s[warp] = __popc(m);
+  if (tid == 0 && p0 + kCompactChunk >= Lin) {
+    int total = 0;
+    for (int i = 0; i < kCompactChunk; ++i) total += dest_s[i] >= 0 ? 1 : 0;
+    ws.cnt[j + 1] = before + total;
   }
-  __syncthreads();
-  const int cnt0 = half_s[0];
-  const int total = half_s[0] + half_s[1];
-  if (tid == 0 && p0 + kCompactChunk >= Lin) ws.cnt[j + 1] = before + total;
-  // one warp per row, 8 rows per warp
+  const int M4 = ws.Mp / 4;
   for (int i = warp; i < kCompactChunk; i += 8) {
     const int r = dest_s[i];
     if (r < 0) continue;
-    const int dest = before + r + (i >= 32 ? cnt0 : 0);
+    const int dest = before + r;
     const int id = in[p0 + i];
     if (lane == 0) {
       out[dest] = id;
       ws.cand1[dest] = 0ull;
     }
-    const float* src = ws.R32 + static_cast<size_t>(id) * ws.Mp;
+    const float4* src = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
           static_cast<__nv_bfloat16*>(ws.Rq[j & 1]) + static_cast<size_t>(dest) * ws.Mp);
-      for (int m = lane; m < ws.Mp / 4; m += 32) {
-        const float4 v = reinterpret_cast<const float4*>(src)[m];
-        dst[2 * m] = __floats2bfloat162_rn(v.x, v.y);
-        dst[2 * m + 1] = __floats2bfloat162_rn(v.z, v.w);
+      for (int m0 = 0; m0 < M4; m0 += 256) {
+        float4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = m0 + t * 32 + lane;
+          v[t] = m < M4 ? src[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = m0 + t * 32 + lane;
+          if (m < M4) {
+            dst[2 * m] = __floats2bfloat162_rn(v[t].x, v[t].y);
+            dst[2 * m + 1] = __floats2bfloat162_rn(v[t].z, v[t].w);
+          }
+        }
       }
     } else if (ws.prec == OMP_PREC_FP8_E4M3) {
       float amax = 0.f;
-      for (int m = lane; m < ws.Mp / 4; m += 32) {
-        const float4 v = reinterpret_cast<const float4*>(src)[m];
-        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      for (int m0 = 0; m0 < M4; m0 += 256) {
+        float4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = m0 + t * 32 + lane;
+          v[t] = m < M4 ? src[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[t].x), fabsf(v[t].y)), fmaxf(fabsf(v[t].z), fabsf(v[t].w))));
       }
       amax = warp_max(amax);
       const float inv = amax > 0.f ? 448.f / amax : 0.f;
       if (lane == 0) ws.sr[j & 1][dest] = amax > 0.f ? amax / 448.f : 0.f;
       uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws.Rq[j & 1]) +
                                                   static_cast<size_t>(dest) * ws.Mp);
-      for (int m = lane; m < ws.Mp / 4; m += 32) {
-        const float4 v = reinterpret_cast<const float4*>(src)[m];
-        const uint32_t b0 = __nv_cvt_float_to_fp8(v.x * inv, __NV_SATFINITE, __NV_E4M3);
-        const uint32_t b1 = __nv_cvt_float_to_fp8(v.y * inv, __NV_SATFINITE, __NV_E4M3);
-        const uint32_t b2 = __nv_cvt_float_to_fp8(v.z * inv, __NV_SATFINITE, __NV_E4M3);
-        const uint32_t b3 = __nv_cvt_float_to_fp8(v.w * inv, __NV_SATFINITE, __NV_E4M3);
-        dst[m] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+      for (int m0 = 0; m0 < M4; m0 += 256) {
+        float4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = m0 + t * 32 + lane;
+          v[t] = m < M4 ? src[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int m = m0 + t * 32 + lane;
+          if (m < M4) {
+            const uint32_t b0 = __nv_cvt_float_to_fp8(v[t].x * inv, __NV_SATFINITE, __NV_E4M3);
+            const uint32_t b1 = __nv_cvt_float_to_fp8(v[t].y * inv, __NV_SATFINITE, __NV_E4M3);
+            const uint32_t b2 = __nv_cvt_float_to_fp8(v[t].z * inv, __NV_SATFINITE, __NV_E4M3);
+            const uint32_t b3 = __nv_cvt_float_to_fp8(v[t].w * inv, __NV_SATFINITE, __NV_E4M3);
+            dst[m] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+          }
+        }
       }
     }
   }

@@ -33,6 +33,13 @@ from workloads import gen  # noqa: E402
 
 WORKLOAD = "gaussian_1024x8192_s32_b4096"
 METRIC = "OMP signals/s, chosen form vs plain FP32 on same GB300 at matched support; % roofline"
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the same
+# kernel source at full live count (profiles/<kernel>_<workload>.md gives the command); ncu
+# flushes the caches before the capture, so this is the cold-cache traffic of one launch. An
+# entry is removed whenever its kernel changes.
+MEASURED_TRAFFIC = {
+    ("gaussian_1024x8192_s32_b4096", "bf16", "correlate"): 25272064.0,
+}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts)
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -261,8 +268,9 @@ def run_gpu(args):
             peak_src
         kern = "update"
         alg = float(upd_bytes.mean())
+    traffic = MEASURED_TRAFFIC.get((w.name, args.precision, kern))
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "kernel": kern,
+                "frac": achieved / peak, "traffic": traffic, "kernel": kern,
                 "peak_source": src, "algorithmic_per_launch": alg,
                 "launch_ms": float(dur * 1e3),
                 "corr_ms_per_step": float(corr_ms.sum()), "update_ms_per_step": float(upd_ms.sum())}

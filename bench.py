@@ -37,6 +37,7 @@ METRIC = "OMP signals/s, chosen form vs plain FP32 on same GB300 at matched supp
 # kernel source at full live count (profiles/<kernel>_<workload>.md gives the command); ncu
 # flushes the caches before the capture, so this is the cold-cache traffic of one launch. An
 # entry is removed whenever its kernel changes.
+L2_RESIDENT_BYTES = 64 << 20   # an FP32 dictionary up to half the 129 MB L2 stays resident
 MEASURED_TRAFFIC = {
     ("gaussian_1024x8192_s32_b4096", "bf16", "correlate"): 25272064.0,
 }
@@ -232,6 +233,9 @@ def run_gpu(args):
         chosen = bench_form(args.precision)
     plain = bench_form("fp32") if args.precision != "fp32" and not args.skip_plain else None
     clocks = clk.summary()
+    # L2-to-SM streaming read bandwidth (the library's probe kernel, 64 MiB buffer), measured
+    # after the timed work: the update kernel's roofline when the FP32 dictionary fits in L2
+    l2_gbs = omp.read_bandwidth_gbs(64, 50)
 
     if rank != 0:
         if world > 1:
@@ -269,11 +273,17 @@ def run_gpu(args):
         kern = "update"
         alg = float(upd_bytes.mean())
     traffic = MEASURED_TRAFFIC.get((w.name, args.precision, kern))
+    mp = (w.M + 63) // 64 * 64
+    a32_bytes = w.N * mp * 4
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "kernel": kern,
                 "peak_source": src, "algorithmic_per_launch": alg,
                 "launch_ms": float(dur * 1e3),
                 "corr_ms_per_step": float(corr_ms.sum()), "update_ms_per_step": float(upd_ms.sum())}
+    if kern == "update" and a32_bytes <= L2_RESIDENT_BYTES:
+        # the gathered atom rows come from L2: the HBM fraction above overstates the kernel
+        roofline["l2_read_peak_gbs"] = l2_gbs
+        roofline["l2_frac"] = achieved / l2_gbs
     e2e_value = B_all * chosen["e2e_steps"] / chosen["e2e_s"]
     line = {
         "metric": METRIC,

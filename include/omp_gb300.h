@@ -196,6 +196,15 @@ omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_o
  * `stream`. */
 omp_status omp_loop_passes(omp_handle h, int32_t* passes_out, void* stream);
 
+/* Measurement helper (no part of the method): `blocks` blocks of 512 threads read the device
+ * buffer `buf` (`bytes` a multiple of 16, 16-byte aligned) `reps` times with L2-only loads and
+ * write one float per block to block_out[0..blocks). Timed around a buffer that fits in L2 it
+ * gives the L2-to-SM read bandwidth the benchmark uses as the roofline of the update kernel when
+ * the FP32 dictionary is L2-resident. Enqueued on `stream`; returns OMP_ERR_INVALID_ARGUMENT for
+ * bad arguments, OMP_ERR_CUDA if the launch fails. */
+omp_status omp_read_bandwidth_probe(const void* buf, int64_t bytes, int32_t reps, float* block_out,
+                                    int32_t blocks, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Learned proposal. A small network maps the first correlation of a signal,
  *   x_n = <y, a_n> / (||a_n|| ||y||)                          (BF16 features)

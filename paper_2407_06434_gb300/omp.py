@@ -37,7 +37,7 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
            "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
-           "omp_loop_passes"]
+           "omp_loop_passes", "omp_read_bandwidth_probe"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -93,6 +93,7 @@ def load(path: Optional[str] = None):
         "omp_solve_batch_trace": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P]),
         "omp_handle_info": (_I32, [_P, ctypes.POINTER(omp_desc), ctypes.POINTER(_I32)]),
         "omp_loop_passes": (_I32, [_P, ctypes.POINTER(_I32), _P]),
+        "omp_read_bandwidth_probe": (_I32, [_P, _I64, _I32, _P, _I32, _P]),
         "omp_proposal_desc_default": (None, [ctypes.POINTER(omp_proposal_desc)]),
         "omp_proposal_create": (_I32, [_P, ctypes.POINTER(omp_proposal_desc), ctypes.POINTER(_P)]),
         "omp_proposal_destroy": (_I32, [_P]),
@@ -299,6 +300,29 @@ def omp_loop_passes(h: Handle, stream=None) -> int:
     v = _I32(0)
     _check(load().omp_loop_passes(h.ptr, ctypes.byref(v), _stream(stream)), "omp_loop_passes")
     return v.value
+
+
+def read_bandwidth_gbs(mbytes: int = 64, reps: int = 50, blocks: int = 0, stream=None) -> float:
+    """Streaming L2-only read bandwidth over a device buffer of `mbytes` MiB (best of three runs
+    of `reps` passes, CUDA events); a measurement helper for the benchmark's L2 roofline."""
+    import torch
+    n = mbytes * 1024 * 1024 // 4
+    buf = torch.randn(n, device="cuda")
+    if blocks <= 0:
+        blocks = 4 * torch.cuda.get_device_properties(buf.device).multi_processor_count
+    out = torch.empty(blocks, device=buf.device)
+    lib = load()
+    st = _stream(stream)
+    _check(lib.omp_read_bandwidth_probe(_ptr(buf), n * 4, 2, _ptr(out), blocks, st), "probe")
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib.omp_read_bandwidth_probe(_ptr(buf), n * 4, reps, _ptr(out), blocks, st), "probe")
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return reps * n * 4 / (best / 1e3) / 1e9
 
 
 def omp_synthesize_signals(A, sup, coef, noise, Y_out, stream=None):

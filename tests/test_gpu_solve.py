@@ -353,3 +353,18 @@ def test_autotune_choice_and_cache(tmp_path, monkeypatch):
     assert omp.omp_autotune(s2.h, Ad, Yd, w.S, 0.0, repeats=1) == choice
     assert len(cache.read_text().strip().splitlines()) == 1
     s2.close()
+
+
+def test_read_bandwidth_probe():
+    """The benchmark's L2 read probe reads every word: the per-block sums add up to reps times
+    the buffer's sum; its bandwidth over an L2-resident buffer is positive and finite."""
+    from paper_2407_06434_gb300 import omp
+    buf = torch.arange(1 << 16, dtype=torch.float32, device="cuda") % 7
+    out = torch.zeros(64, device="cuda")
+    st = omp.load().omp_read_bandwidth_probe(buf.data_ptr(), buf.numel() * 4, 3, out.data_ptr(), 64, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert float(out.sum()) == pytest.approx(3 * float(buf.sum()), rel=1e-5)
+    assert omp.load().omp_read_bandwidth_probe(buf.data_ptr(), 12, 1, out.data_ptr(), 64, None) != 0
+    gbs = omp.read_bandwidth_gbs(32, 10)
+    assert np.isfinite(gbs) and gbs > 0

@@ -135,21 +135,35 @@ struct EpiTop8 {
   // A compare-only pass marks the columns whose score beats the threshold; only those are
   // inserted (few per chunk once the list is warm), each read back from the registers with a
   // select tree, so the warp neither diverges per column nor needs a staging buffer. A fresh list
-  // takes the chunk's first 8 columns unconditionally: the smallest of them is a safe threshold
-  // for the rest (at least 8 scores of the chunk reach it).
+  // is seeded, without a per-column loop, with the best column of each group of 4 (lowest index
+  // on ties): those 8 are distinct columns of the chunk, so their smallest score is a safe
+  // threshold for the rest (at least 8 scores reach it), and a high one, which keeps the first
+  // chunk's insertions few.
   __device__ void chunk(int, int t, int c0, const uint32_t (&cur)[32]) {
     const int nb = t * BN + c0;
     const int lim = min(32, ws.N - nb);
     const float* scl = scr + (c0 - part * EPI_COLS);
     const float4* sc4 = reinterpret_cast<const float4*>(scl);
-    int j0 = 0;
+    uint32_t seeded = 0;
     if (ti[0] < 0) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float v = fabsf(__uint_as_float(cur[j])) * scl[j];
-        if (j < lim && v > ts[7]) top8_insert(ts, ti, v, nb + j);  // false only for NaN
+      for (int g = 0; g < 8; ++g) {
+        float bv = -1.f;
+        int bj = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * g + q;
+          const float v = fabsf(__uint_as_float(cur[j])) * scl[j];
+          if (j < lim && v > bv) {  // false for NaN
+            bv = v;
+            bj = j;
+          }
+        }
+        if (bj >= 0) {
+          top8_insert(ts, ti, bv, nb + bj);
+          seeded |= 1u << bj;
+        }
       }
-      j0 = 8;
     }
     // own 8th best, raised to just below each other part's when that one is positive and
     // belongs to the same signal tile (x >= other  <=>  x > its predecessor, for x >= 0)
@@ -172,7 +186,7 @@ struct EpiTop8 {
       mask |= (fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w > thr ? 1u : 0u) << (4 * j4 + 3);
     }
     if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
-    if (j0) mask &= 0xffffff00u;
+    mask &= ~seeded;
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;

@@ -196,6 +196,23 @@ omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_o
  * `stream`. */
 omp_status omp_loop_passes(omp_handle h, int32_t* passes_out, void* stream);
 
+/* Gram-space solve (the v0 family of Sec. 2.3): the same problem as omp_solve_batch_ex, with
+ * no correlation GEMM per step. One FP32 GEMM gives c = A^T y for the batch; then each signal's
+ * block keeps c in shared memory and, per step, picks n* = argmax |c_n| / ||a_n|| (lowest index
+ * on ties), appends the inverse-Cholesky column F_k from the Gram row of n* (gamma in FP64),
+ * takes b_k = gamma c_{n*} and updates c <- c - b_k A^T q_k with A^T q_k = sum_j F[j,k] G[s_j,:].
+ * ||r_k||^2 = ||r_{k-1}||^2 - b_k^2 drives the eps stop (only when eps > 0); at the end
+ * x = F b and the residual y - A_S x is formed once for resid_norm_out. Any precision of the
+ * handle; the handle's Gram matrix (N x N FP32) is used. Pays off when N is small next to M
+ * (per step (k+1) N Gram reads instead of 2 M N FLOPs plus the update's atom-row gathers).
+ * On first use it allocates an N x max_batch FP32 workspace (so the first call is not
+ * graph-capturable). OMP_ERR_INVALID_ARGUMENT also when N floats + S (S + 1) / 2 floats of
+ * per-signal shared memory exceed 227 KB. Outputs as omp_solve_batch_ex (optional ones may be
+ * NULL); enqueued on `stream`. */
+omp_status omp_solve_batch_gram(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                                float* resid_norm_out, int32_t* stop_out, void* stream);
+
 /* Measurement helper (no part of the method): `blocks` blocks of 512 threads read the device
  * buffer `buf` (`bytes` a multiple of 16, 16-byte aligned) `reps` times with L2-only loads and
  * write one float per block to block_out[0..blocks). Timed around a buffer that fits in L2 it

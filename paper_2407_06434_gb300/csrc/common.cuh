@@ -59,6 +59,7 @@ struct Ws {
   float* escale;   // quantised paths: score scale per atom (1/||a|| or s_a/||a||), padded
   double* norm2;
   float* gram;
+  float* c0;        // Bmax x N FP32 first correlation of the Gram-space solve (allocated on use)
   // signal state
   float* R32;
   void* Rq[2];
@@ -186,6 +187,10 @@ __device__ __forceinline__ int tc_piece_count(const Ws& ws, int L, int p) {
 void launch_prep(const Ws& ws, const float* A, cudaStream_t s);
 void launch_gram_simt(const Ws& ws, cudaStream_t s);
 void launch_corr_simt(const Ws& ws, int k, int B, cudaStream_t s);
+void launch_c0_simt(const Ws& ws, int B, cudaStream_t s);
+void launch_gram_solve(const Ws& ws, const CallArgs* args, int B, int S, float eps, int eps_rel,
+                       cudaStream_t s);
+cudaError_t configure_gram_solve(const Ws& ws);
 void launch_init(const Ws& ws, const CallArgs* args, int B, cudaStream_t s);
 void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s);
 void launch_compact(const Ws& ws, int j, int B, int S, cudaStream_t s);

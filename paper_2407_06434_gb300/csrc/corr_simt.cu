@@ -6,6 +6,9 @@
 // A 128 x 128 output tile per 256-thread block, 8 x 8 outputs per thread, K chunks of 16 staged
 // through double-buffered shared memory.
 //
+// A third form stores C = Y A^T for signals 0..B-1 (rows of R32 in signal order) into the c0
+// workspace: the exact first correlation the Gram-space solve starts from.
+//
 // The correlation never writes C: the epilogue forms the score |c| / ||a_n|| (Alg. 1), takes
 // each thread's best atom in ascending index order (strict '>', so the lowest index keeps a
 // tie), reduces across the 16 threads that share a signal with warp shuffles, and merges the
@@ -19,8 +22,12 @@ namespace ompk {
 namespace {
 constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
 
-template <bool GRAM>
+constexpr int kCorrelate = 0, kGram = 1, kStoreC = 2;
+
+// MODE kCorrelate: k is the iteration; kGram: k unused; kStoreC: k is the number of signals
+template <int MODE>
 __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
+  constexpr bool GRAM = MODE == kGram;
   __shared__ __align__(16) float Xs[2][BK][BM + PAD];
   __shared__ __align__(16) float As[2][BK][BN + PAD];
   const int tid = threadIdx.x;
@@ -30,6 +37,8 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
   const int* live = nullptr;
   if (GRAM) {
     L = ws.N;
+  } else if (MODE == kStoreC) {
+    L = k;
   } else {
     k = iter_of(ws, k);
     L = ws.cnt[k + 1];
@@ -45,7 +54,7 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
   for (int i = 0; i < 2; ++i) {
     const int p = p0 + lrow + 64 * i;
     xv[i] = p < L;
-    const int row = xv[i] ? (GRAM ? p : live[p]) : 0;
+    const int row = xv[i] ? ((GRAM || MODE == kStoreC) ? p : live[p]) : 0;
     xsrc[i] = (GRAM ? ws.A32 : ws.R32) + static_cast<size_t>(row) * ws.Mp + lk;
     const int n = n0 + lrow + 64 * i;
     av[i] = n < ws.N;
@@ -123,6 +132,18 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
     }
     return;
   }
+  if (MODE == kStoreC) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+      if (row >= L) continue;
+      float* c = ws.c0 + static_cast<size_t>(row) * ws.N;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (ncol[j] < ws.N) c[ncol[j]] = acc[i][j];
+    }
+    return;
+  }
 
   float inv[8];
 #pragma unroll
@@ -158,12 +179,17 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
 
 void launch_corr_simt(const Ws& ws, int k, int B, cudaStream_t s) {
   dim3 grid((ws.N + BN - 1) / BN, (B + BM - 1) / BM);
-  simt_tile_kernel<false><<<grid, 256, 0, s>>>(ws, k);
+  simt_tile_kernel<kCorrelate><<<grid, 256, 0, s>>>(ws, k);
+}
+
+void launch_c0_simt(const Ws& ws, int B, cudaStream_t s) {
+  dim3 grid((ws.N + BN - 1) / BN, (B + BM - 1) / BM);
+  simt_tile_kernel<kStoreC><<<grid, 256, 0, s>>>(ws, B);
 }
 
 void launch_gram_simt(const Ws& ws, cudaStream_t s) {
   dim3 grid((ws.N + BN - 1) / BN, (ws.N + BM - 1) / BM);
-  simt_tile_kernel<true><<<grid, 256, 0, s>>>(ws, 0);
+  simt_tile_kernel<kGram><<<grid, 256, 0, s>>>(ws, 0);
 }
 
 }  // namespace ompk

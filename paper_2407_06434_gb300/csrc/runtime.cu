@@ -464,6 +464,40 @@ omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, i
   return run_solve(h, static_cast<int>(B), S, eps, s);
 }
 
+omp_status omp_solve_batch_gram(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
+                                float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
+                                float* resid_norm_out, int32_t* stop_out, void* stream) {
+  omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
+  if (st != OMP_OK) return st;
+  DeviceGuard guard(h->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->ws.c0) {  // first use: the first-correlation workspace and the kernel's shared memory
+    if (configure_gram_solve(h->ws) != cudaSuccess) {
+      cudaGetLastError();
+      return OMP_ERR_INVALID_ARGUMENT;
+    }
+    if (!dalloc(h, &h->ws.c0, static_cast<size_t>(h->ws.Bmax) * h->ws.N)) return OMP_ERR_OUT_OF_MEMORY;
+  }
+  if (A != h->prepared_A) {
+    st = prepare(h, A, s);
+    if (st != OMP_OK) return st;
+  }
+  CallArgs a{};
+  a.Y = Y;
+  a.X = X_out;
+  a.support = support_out;
+  a.n_iter = n_iter_out;
+  a.resid = resid_norm_out;
+  a.stop = stop_out;
+  launch_set_args(h->args_dev, a, s);
+  const Ws& ws = h->ws;
+  launch_init(ws, h->args_dev, static_cast<int>(B), s);
+  launch_c0_simt(ws, static_cast<int>(B), s);
+  launch_gram_solve(ws, h->args_dev, static_cast<int>(B), S, eps, h->d.eps_relative, s);
+  launch_finalize(ws, h->args_dev, static_cast<int>(B), S, s);
+  return check_launch();
+}
+
 namespace {
 omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
                             omp_proposal p, const int32_t* cand, int32_t K, const float* tau, float* X_out,

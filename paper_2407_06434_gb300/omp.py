@@ -37,7 +37,7 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
            "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
-           "omp_loop_passes", "omp_read_bandwidth_probe"]
+           "omp_loop_passes", "omp_read_bandwidth_probe", "omp_solve_batch_gram"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -93,6 +93,7 @@ def load(path: Optional[str] = None):
         "omp_solve_batch_trace": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P]),
         "omp_handle_info": (_I32, [_P, ctypes.POINTER(omp_desc), ctypes.POINTER(_I32)]),
         "omp_loop_passes": (_I32, [_P, ctypes.POINTER(_I32), _P]),
+        "omp_solve_batch_gram": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
         "omp_read_bandwidth_probe": (_I32, [_P, _I64, _I32, _P, _I32, _P]),
         "omp_proposal_desc_default": (None, [ctypes.POINTER(omp_proposal_desc)]),
         "omp_proposal_create": (_I32, [_P, ctypes.POINTER(omp_proposal_desc), ctypes.POINTER(_P)]),
@@ -214,6 +215,16 @@ def omp_solve_batch_ex(h: Handle, A, Y, S: int, eps: float, X_out, support_out, 
     _check(load().omp_solve_batch_ex(h.ptr, _ptr(A), _ptr(Y), B, S, eps, _ptr(X_out),
                                      _ptr(support_out), _ptr(n_iter_out), _ptr(resid_norm_out),
                                      _ptr(stop_out), _stream(stream)), "omp_solve_batch_ex")
+
+
+def omp_solve_batch_gram(h: Handle, A, Y, S: int, eps: float, X_out, support_out, n_iter_out=None,
+                         resid_norm_out=None, stop_out=None, stream=None):
+    """Gram-space solve (no correlation GEMM per step); outputs as omp_solve_batch_ex."""
+    _check_A(A, h.M, h.N)
+    B = Y.shape[0]
+    _check(load().omp_solve_batch_gram(h.ptr, _ptr(A), _ptr(Y), B, S, eps, _ptr(X_out),
+                                       _ptr(support_out), _ptr(n_iter_out), _ptr(resid_norm_out),
+                                       _ptr(stop_out), _stream(stream)), "omp_solve_batch_gram")
 
 
 def omp_solve_batch_host(h: Handle, A, Y_host, S: int, eps: float, X_host, support_host,
@@ -441,6 +452,18 @@ class OmpSolver:
 
     def __init__(self, M, N, max_batch=4096, max_iters=64, precision="bf16", **kw):
         self.h = omp_create(M, N, max_batch, max_iters, precision, **kw)
+
+    def solve_gram(self, A, Y, S, eps=0.0, stream=None, diagnostics=False):
+        """The Gram-space solve of the same batch (see omp_solve_batch_gram)."""
+        import torch
+        B = Y.shape[0]
+        X = torch.empty((B, S), dtype=torch.float32, device=Y.device)
+        sup = torch.empty((B, S), dtype=torch.int32, device=Y.device)
+        n_iter = torch.empty(B, dtype=torch.int32, device=Y.device)
+        resid = torch.empty(B, dtype=torch.float32, device=Y.device)
+        stop = torch.empty(B, dtype=torch.int32, device=Y.device)
+        omp_solve_batch_gram(self.h, A, Y, S, eps, X, sup, n_iter, resid, stop, stream)
+        return (X, sup, n_iter, resid, stop) if diagnostics else (X, sup)
 
     def solve(self, A, Y, S, eps=0.0, stream=None, diagnostics=False):
         import torch

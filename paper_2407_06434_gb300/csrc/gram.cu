@@ -2,7 +2,8 @@
 // updated through the Gram matrix instead of a correlation GEMM per step), for dictionaries
 // whose Gram matrix is small (N up to a few thousand atoms, so G = A^T A stays in L2).
 //
-// One warp runs all iterations of one signal:
+// One block of W warps (W = 1 up to 1536 atoms, 8 for larger N) runs all iterations of one
+// signal:
 //   c      = A^T y                           FP32, from one batched SIMT GEMM before the loop
 //   per step k (0-based; the paper's k+1):
 //     n*   = argmax_n |c_n| / ||a_n||        lowest atom index on ties (Alg. 1)
@@ -21,18 +22,20 @@
 //
 // Per signal and step the work is (k+1) N FMAs on Gram rows read from L2 (shared by all
 // signals), against the dense loop's 2 M N tensor-core FLOPs, 8 rescoring rows and k+1 gathered
-// atom rows of M floats: the Gram form wins when N is small next to M. A warp per signal keeps
-// about 32 signals resident per SM (shared memory permitting), which the Gram-row reads need to
-// reach L2 bandwidth: one signal's chain of dependent steps leaves its warp mostly waiting.
+// atom rows of M floats: the Gram form wins when N is small next to M. Small blocks keep many
+// signals resident per SM (shared memory permitting), which the Gram-row reads need to reach L2
+// bandwidth, since one signal's chain of dependent steps leaves its warps mostly waiting; a
+// larger N shortens each signal's argmax and c update with more warps.
 #include "common.cuh"
 
 namespace ompk {
 namespace {
 
-constexpr int kWarpsPerBlock = 1;  // one signal per block: residency is set by registers and smem
-constexpr int kPanel = 512;        // atoms per pass of the c update: 4 float4 per lane
 
 struct GSmem {
+  double* rd;  // 9: block reduction scratch
+  float* rs;   // 8: per-warp best scores
+  int* ri;     // 9: per-warp best atoms, then the block's
   float* c;    // Np4: current correlations (N rounded up to 4, tail zero)
   float* Fs;   // S (S + 1) / 2: FP32 copy of the packed factor, column j at j (j + 1) / 2
   float* w;    // S: Gram row of n* at the support
@@ -44,14 +47,18 @@ struct GSmem {
 __host__ __device__ __forceinline__ int np4(int N) { return (N + 3) / 4 * 4; }
 
 __host__ __device__ __forceinline__ size_t gs_bytes(int N, int S) {
-  size_t b = static_cast<size_t>(np4(N)) * 4 + static_cast<size_t>(S) * (S + 1) / 2 * 4 +
-             static_cast<size_t>(S) * 4 * 2 + static_cast<size_t>(S + 1) * 4 + static_cast<size_t>(S) * 4;
+  size_t b = 9 * 8 + 8 * 4 + 9 * 4 + 4 + static_cast<size_t>(np4(N)) * 4 +
+             static_cast<size_t>(S) * (S + 1) / 2 * 4 + static_cast<size_t>(S) * 4 * 2 +
+             static_cast<size_t>(S + 1) * 4 + static_cast<size_t>(S) * 4;
   return (b + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ GSmem gs_layout(unsigned char* base, int N, int S) {
   GSmem g;
-  g.c = reinterpret_cast<float*>(base);
+  g.rd = reinterpret_cast<double*>(base);
+  g.rs = reinterpret_cast<float*>(base + 9 * 8);
+  g.ri = reinterpret_cast<int*>(g.rs + 8);
+  g.c = reinterpret_cast<float*>(base + 9 * 8 + 8 * 4 + 9 * 4 + 4);  // 16-byte aligned
   g.Fs = g.c + np4(N);
   g.w = g.Fs + static_cast<size_t>(S) * (S + 1) / 2;
   g.z = g.w + S;
@@ -60,20 +67,45 @@ __device__ __forceinline__ GSmem gs_layout(unsigned char* base, int N, int S) {
   return g;
 }
 
+template <int W>
+__device__ __forceinline__ void bsync() {
+  if (W == 1)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+// Sum over the block's W warps; every thread gets the total.
+template <int W>
+__device__ __forceinline__ double bsum(double v, double* red) {
+  v = warp_sum(v);
+  if (W == 1) return v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
 // ||y - A_S x||^2 for the first n picks, x = F b (FP64 back-substitution into g.z); with `store`
-// the residual replaces y in R32. Called by the whole warp.
+// the residual replaces y in R32. Called by the whole block.
+template <int W>
 __device__ double residual_norm2(const Ws& ws, const GSmem& g, const double* Fg, const double* bvg,
-                                 int b, int n, bool store, int lane) {
-  for (int i = lane; i < n; i += 32) {
+                                 int b, int n, bool store) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += 32 * W) {
     double acc = 0.0;
     for (int j = i; j < n; ++j) acc += Fg[static_cast<size_t>(j) * (j + 1) / 2 + i] * bvg[j];
     g.z[i] = static_cast<float>(acc);
   }
-  __syncwarp();
+  bsync<W>();
   const int M4 = ws.Mp >> 2;
   float4* rg = reinterpret_cast<float4*>(ws.R32 + static_cast<size_t>(b) * ws.Mp);  // holds y
   double rr = 0.0;
-  for (int q = lane; q < M4; q += 32) {
+  for (int q = tid; q < M4; q += 32 * W) {
     float4 r = rg[q];
     for (int i = 0; i < n; ++i) {
       const float4 a = __ldg(reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(g.sup[i]) * ws.Mp) + q);
@@ -87,18 +119,22 @@ __device__ double residual_norm2(const Ws& ws, const GSmem& g, const double* Fg,
     rr += static_cast<double>(r.x) * r.x + static_cast<double>(r.y) * r.y +
           static_cast<double>(r.z) * r.z + static_cast<double>(r.w) * r.w;
   }
-  __syncwarp();
-  return warp_sum(rr);
+  bsync<W>();
+  return bsum<W>(rr, g.rd);
 }
 
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, int B, int S, float eps,
-                                                                        int eps_rel) {
+template <int W>
+__global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S, float eps, int eps_rel) {
+  constexpr int T = 32 * W;
+  // c update shape: a lone warp keeps 4 float4 accumulators and 2 Gram rows in flight; wider
+  // blocks spread the atoms thinner (one float4 per thread) and keep 8 rows in flight
+  constexpr int VP = W == 1 ? 4 : 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int b = blockIdx.x * kWarpsPerBlock + wib;
-  if (b >= B) return;  // the whole warp leaves; warps of a block never wait on each other
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  if (b >= B) return;  // the whole block leaves
   const int N = ws.N;
-  GSmem g = gs_layout(smem + static_cast<size_t>(wib) * gs_bytes(N, S), N, S);
+  GSmem g = gs_layout(smem, N, S);
   const float yn = ws.ynorm[b];
   // y == 0 or non-finite: the init kernel left an empty support (stop code 3)
   if (!(yn > 0.f) || ws.flag[b] == 0) return;
@@ -107,8 +143,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
   double* Fg = ws.F + static_cast<size_t>(b) * ws.Fstride;
   float* Ff = ws.F32 + static_cast<size_t>(b) * ws.Fstride;
   const float* c0 = ws.c0 + static_cast<size_t>(b) * N;
-  for (int n = lane; n < np4(N); n += 32) g.c[n] = n < N ? c0[n] : 0.f;
-  __syncwarp();
+  for (int n = tid; n < np4(N); n += T) g.c[n] = n < N ? c0[n] : 0.f;
+  bsync<W>();
   const bool vec = (N & 3) == 0;  // Gram rows start 16-byte aligned
 
   double r2 = static_cast<double>(yn) * static_cast<double>(yn);
@@ -116,11 +152,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
   int k = 0;
   int stop = kStopIters;
   for (; k < S; ++k) {
-    // ---- n* = argmax |c_n| / ||a_n||: lane l scans atoms 4l + 128p + {0..3}, ascending with a
-    // strict '>' (lowest index first), then the warp reduction keeps the lower index on ties
+    // ---- n* = argmax |c_n| / ||a_n||: thread t scans atoms 4t + 4Tp + {0..3}, ascending with a
+    // strict '>' (lowest index first), then the reductions keep the lower index on ties
     float bs = -1.f;
     int bi = 0x7fffffff;
-    for (int n0 = 4 * lane; n0 < N; n0 += 128) {
+    for (int n0 = 4 * tid; n0 < N; n0 += 4 * T) {
       const float4 cv = *reinterpret_cast<const float4*>(g.c + n0);
       const float cq[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
@@ -144,37 +180,51 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
         bi = oi;
       }
     }
+    if (W > 1) {
+      if (lane == 0) {
+        g.rs[warp] = bs;
+        g.ri[warp] = bi;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (better(g.rs[i], g.ri[i], bs, bi)) {
+          bs = g.rs[i];
+          bi = g.ri[i];
+        }
+      __syncthreads();
+    }
     const int ns = bi;
     if (ns < 0 || ns >= N) {  // no finite score
-      if (lane == 0) atomicOr(ws.err, OMP_DEVERR_BAD_STATE);
+      if (tid == 0) atomicOr(ws.err, OMP_DEVERR_BAD_STATE);
       break;
     }
     // ---- w_i = G[n*, s_i]
     const float* grow = ws.gram + static_cast<size_t>(ns) * N;
-    for (int i = lane; i < k; i += 32) g.w[i] = __ldg(grow + g.sup[i]);
+    for (int i = tid; i < k; i += T) g.w[i] = __ldg(grow + g.sup[i]);
     const double nrm2 = ws.norm2[ns];
     const float cn = g.c[ns];
-    __syncwarp();
-    // ---- z_j = sum_{i<=j} F[i,j] w_i (lane j, j + 32, ...), ||z||^2 in FP64
+    bsync<W>();
+    // ---- z_j = sum_{i<=j} F[i,j] w_i (thread j, j + T, ...), ||z||^2 in FP64
     double zz = 0.0;
-    for (int j = lane; j < k; j += 32) {
+    for (int j = tid; j < k; j += T) {
       const float* col = g.Fs + static_cast<size_t>(j) * (j + 1) / 2;
       float zj = 0.f;
       for (int i = 0; i <= j; ++i) zj = fmaf(col[i], g.w[i], zj);
       g.z[j] = zj;
       zz += static_cast<double>(zj) * zj;
     }
-    zz = warp_sum(zz);
+    zz = bsum<W>(zz, g.rd);  // (its barrier also publishes z)
     const double delta = nrm2 - zz;
     if (!(delta > kDepRtol * nrm2)) {
       stop = kStopDependent;
       break;
     }
     const double gamma = 1.0 / sqrt(delta);
-    __syncwarp();
-    // ---- F[:,k] = [-gamma F z ; gamma]: u_i = sum_{j>=i} F[i,j] z_j (lane i, i + 32, ...)
+    bsync<W>();
+    // ---- F[:,k] = [-gamma F z ; gamma]: u_i = sum_{j>=i} F[i,j] z_j (thread i, i + T, ...)
     const size_t off = static_cast<size_t>(k) * (k + 1) / 2;
-    for (int i = lane; i < k; i += 32) {
+    for (int i = tid; i < k; i += T) {
       float u = 0.f;
       for (int j = i; j < k; ++j) u = fmaf(g.Fs[static_cast<size_t>(j) * (j + 1) / 2 + i], g.z[j], u);
       const double fv = -gamma * static_cast<double>(u);
@@ -184,7 +234,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
       Fg[off + i] = fv;
       Ff[off + i] = f32;
     }
-    if (lane == 0) {
+    if (tid == 0) {
       const float gf = static_cast<float>(gamma);
       g.f[k] = gf;
       g.Fs[off + k] = gf;
@@ -193,22 +243,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
       g.sup[k] = ns;
       supg[k] = ns;
     }
-    __syncwarp();
+    bsync<W>();
     const double bk = gamma * static_cast<double>(cn);
-    // ---- c <- c - b_k sum_j f_j G[s_j, :], in panels of kPanel atoms: lane l takes 4 atoms
-    // per 128, 16-byte Gram loads (scalar ones when N is not a multiple of 4)
+    // ---- c <- c - b_k sum_j f_j G[s_j, :], in panels: thread t takes 4 atoms per 4T, 16-byte
+    // Gram loads (scalar ones when N is not a multiple of 4)
     const float bf = static_cast<float>(bk);
-    for (int p0 = 0; p0 < N; p0 += kPanel) {
-      float4 acc[kPanel / 128];
+    for (int p0 = 0; p0 < N; p0 += 4 * T * VP) {
+      float4 acc[VP];
 #pragma unroll
-      for (int t = 0; t < kPanel / 128; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
+      for (int t = 0; t < VP; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll (W == 1 ? 2 : 8)
       for (int a = 0; a <= k; ++a) {
         const float fa = g.f[a];
         const float* gr = ws.gram + static_cast<size_t>(g.sup[a]) * N;
 #pragma unroll
-        for (int t = 0; t < kPanel / 128; ++t) {
-          const int n0 = p0 + 128 * t + 4 * lane;
+        for (int t = 0; t < VP; ++t) {
+          const int n0 = p0 + 4 * T * t + 4 * tid;
           if (n0 < N) {
             float4 gv;
             if (vec) {
@@ -227,8 +277,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
         }
       }
 #pragma unroll
-      for (int t = 0; t < kPanel / 128; ++t) {
-        const int n0 = p0 + 128 * t + 4 * lane;
+      for (int t = 0; t < VP; ++t) {
+        const int n0 = p0 + 4 * T * t + 4 * tid;
         if (n0 < N) {
           float4* cp = reinterpret_cast<float4*>(g.c + n0);
           float4 cv = *cp;
@@ -242,15 +292,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
     }
     const double r2prev = r2;
     r2 -= bk * bk;
-    if (lane == 0) {
+    if (tid == 0) {
       bvg[k] = bk;
       ws.drop[static_cast<size_t>(b) * ws.Smax + k] = r2prev > 0.0 ? static_cast<float>((bk * bk) / r2prev) : 0.f;
     }
-    __syncwarp();  // c updated before the next selection
+    bsync<W>();  // c updated before the next selection
     // The running ||r||^2 carries the FP32 error of the b_k (about k 2^-24 ||y||^2), so near
     // the threshold the stop test uses the residual itself, formed from the support.
     if (thr > 0.0 && r2 <= 4.0 * thr * thr + 2e-5 * static_cast<double>(yn) * yn) {
-      const double rr = residual_norm2(ws, g, Fg, bvg, b, k + 1, false, lane);
+      const double rr = residual_norm2<W>(ws, g, Fg, bvg, b, k + 1, false);
       if (rr <= thr * thr) {
         stop = kStopEps;
         ++k;
@@ -261,8 +311,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
 
   // ---- x = F b, r = y - A_S x (stored) and its norm
   const int n_it = k;
-  const double rr = residual_norm2(ws, g, Fg, bvg, b, n_it, true, lane);
-  if (lane == 0) {
+  const double rr = residual_norm2<W>(ws, g, Fg, bvg, b, n_it, true);
+  if (tid == 0) {
     ws.niter[b] = n_it;
     ws.rnorm[b] = static_cast<float>(sqrt(rr));
     ws.stop[b] = stop;
@@ -270,19 +320,37 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) gram_solve_kernel(Ws ws, 
   }
 }
 
+// warps per signal for a dictionary of N atoms
+int gram_warps(int N) { return N <= 1536 ? 1 : 8; }
+
+template <int W>
+cudaError_t set_attr(size_t bytes) {
+  return cudaFuncSetAttribute(gram_solve_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(bytes));
+}
+
 }  // namespace
 
 cudaError_t configure_gram_solve(const Ws& ws) {
-  const size_t bytes = gs_bytes(ws.N, ws.Smax) * kWarpsPerBlock;
+  const size_t bytes = gs_bytes(ws.N, ws.Smax);
   if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(gram_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(bytes));
+  switch (gram_warps(ws.N)) {
+    case 1: return set_attr<1>(bytes);
+    case 2: return set_attr<2>(bytes);
+    case 4: return set_attr<4>(bytes);
+    default: return set_attr<8>(bytes);
+  }
 }
 
 void launch_gram_solve(const Ws& ws, const CallArgs*, int B, int S, float eps, int eps_rel,
                        cudaStream_t s) {
-  gram_solve_kernel<<<(B + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
-                      gs_bytes(ws.N, S) * kWarpsPerBlock, s>>>(ws, B, S, eps, eps_rel);
+  const size_t smem = gs_bytes(ws.N, S);
+  switch (gram_warps(ws.N)) {
+    case 1: gram_solve_kernel<1><<<B, 32, smem, s>>>(ws, B, S, eps, eps_rel); break;
+    case 2: gram_solve_kernel<2><<<B, 64, smem, s>>>(ws, B, S, eps, eps_rel); break;
+    case 4: gram_solve_kernel<4><<<B, 128, smem, s>>>(ws, B, S, eps, eps_rel); break;
+    default: gram_solve_kernel<8><<<B, 256, smem, s>>>(ws, B, S, eps, eps_rel); break;
+  }
 }
 
 }  // namespace ompk

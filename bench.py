@@ -62,6 +62,25 @@ def dist_env():
     return rank, world, local
 
 
+def rank_batch(w, A, rank: int):
+    """Rank r's shard of a weak-scaling run: the workload's batch drawn with seed r, so rank 0
+    solves exactly the single-GPU batch and every rank a distinct one of the same shape (signals
+    are independent, so ranks share no data and need no collective on the solve path)."""
+    Y, *_ = gen.signals(w, A, seed=rank)
+    return Y
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's value (the whole job ends with it); the identity on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_cores():
     try:
         from threadpoolctl import threadpool_info
@@ -158,7 +177,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     w = gen.get_config(args.config)
     A = gen.dictionary(w)
-    Y, *_ = gen.signals(w, A)
+    Y = rank_batch(w, A, rank)
     Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
     Yd = torch.from_numpy(Y).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -190,11 +209,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier()
         ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        total = sum(ms)
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(sum(ms), world, dev)
         # instrumented replay: per-launch durations of correlation and update kernels
         omp.omp_profile_enable(h, True)
         corr = np.zeros(w.S)

@@ -358,6 +358,29 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   for (int t = 0; t < V; ++t) q[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int na = kk + 1;
   int a = 0;
+  // r is not needed during the gather (it is read again below), so its registers carry a third
+  // row in flight
+  for (; a + 3 <= na; a += 3) {
+    const float f0 = gs.f[a], f1 = gs.f[a + 1], f2 = gs.f[a + 2];
+    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
+    const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 1]) * ws.Mp);
+    const float4* a2 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 2]) * ws.Mp);
+    float4 v0[V], v1[V], v2[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = t * (W * 32) + wig * 32 + lane;
+      v0[t] = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v1[t] = s < M4 ? __ldg(a1 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v2[t] = s < M4 ? __ldg(a2 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      q[t].x = fmaf(f2, v2[t].x, fmaf(f1, v1[t].x, fmaf(f0, v0[t].x, q[t].x)));
+      q[t].y = fmaf(f2, v2[t].y, fmaf(f1, v1[t].y, fmaf(f0, v0[t].y, q[t].y)));
+      q[t].z = fmaf(f2, v2[t].z, fmaf(f1, v1[t].z, fmaf(f0, v0[t].z, q[t].z)));
+      q[t].w = fmaf(f2, v2[t].w, fmaf(f1, v1[t].w, fmaf(f0, v0[t].w, q[t].w)));
+    }
+  }
   for (; a + 2 <= na; a += 2) {
     const float f0 = gs.f[a], f1 = gs.f[a + 1];
     const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
@@ -389,6 +412,11 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       q[t].z = fmaf(f0, v.z, q[t].z);
       q[t].w = fmaf(f0, v.w, q[t].w);
     }
+  }
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int s = t * (W * 32) + wig * 32 + lane;
+    r[t] = s < M4 ? rrow[s] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   float bp = 0.f;
 #pragma unroll

@@ -489,6 +489,21 @@ def run_learned(args):
         t_plain = timed(lambda: omp.omp_solve_batch(plain.h, Ad, Yd, w.S, w.eps, X, sup))
         sup_p = sup.cpu().numpy()
     clocks = clk.summary()
+    # end to end: the batch from pinned host memory, the learned solve, X and supports back
+    Yh = torch.from_numpy(Y).pin_memory()
+    Xh = torch.empty((w.B, w.S), dtype=torch.float32).pin_memory()
+    Sh = torch.empty((w.B, w.S), dtype=torch.int32).pin_memory()
+    e2e = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Yg = Yh.to(dev, non_blocking=True)
+        omp.omp_solve_batch_learned(dense.h, p, Ad, Yg, w.S, w.eps, X, sup, n_iter, resid, fb)
+        Xh.copy_(X, non_blocking=True)
+        Sh.copy_(sup, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
     rec = lambda S_: float(np.mean([set(S_[b][S_[b] >= 0]) == set(planted[b]) for b in range(w.B)]))
     value = w.B * args.steps / (t_learned / 1e3)
     line = {
@@ -500,6 +515,8 @@ def run_learned(args):
                    "M": w.M, "N": w.N, "B": w.B, "S": w.S, "l2": "flushed between timed steps",
                    "train_signals": args.train_signals, "train_epochs": args.train_epochs},
         "clocks": clocks,
+        "e2e": {"value": w.B * len(e2e) / float(np.sum(e2e)), "unit": "signals/s",
+                "h2d_bytes_per_step": int(Y.nbytes), "d2h_bytes_per_step": int(w.B * w.S * 8)},
         "learned": {"fallback_rate": float(np.mean(fb_l >= 0)),
                     "mean_fallback_step": float(np.mean(fb_l[fb_l >= 0])) if np.any(fb_l >= 0) else None,
                     "planted_recovery": rec(sup_l), "support_equal_to_plain": float(np.mean(np.all(sup_l == sup_p, axis=1))),

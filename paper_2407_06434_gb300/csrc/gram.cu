@@ -2,7 +2,8 @@
 // updated through the Gram matrix instead of a correlation GEMM per step), for dictionaries
 // whose Gram matrix is small (N up to a few thousand atoms, so G = A^T A stays in L2).
 //
-// One block of W warps (W = 1 up to 1536 atoms, 8 for larger N) runs all iterations of one
+// One block of W warps (W = 1 for up to 1536 atoms and a batch of at least 32 signals per SM,
+// 8 otherwise) runs all iterations of one
 // signal:
 //   c      = A^T y                           FP32, from one batched SIMT GEMM before the loop
 //   per step k (0-based; the paper's k+1):
@@ -320,8 +321,10 @@ __global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S,
   }
 }
 
-// warps per signal for a dictionary of N atoms
-int gram_warps(int N) { return N <= 1536 ? 1 : 8; }
+// warps per signal: one for small dictionaries when the batch fills the GPU with one-warp
+// signals (16 per SM), eight otherwise (a larger N shortens each signal's argmax and c update;
+// a small batch needs the parallelism within each signal)
+int gram_warps(int N, int B, int sms) { return (N <= 1536 && B >= 2 * 16 * sms) ? 1 : 8; }
 
 template <int W>
 cudaError_t set_attr(size_t bytes) {
@@ -334,23 +337,17 @@ cudaError_t set_attr(size_t bytes) {
 cudaError_t configure_gram_solve(const Ws& ws) {
   const size_t bytes = gs_bytes(ws.N, ws.Smax);
   if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-  switch (gram_warps(ws.N)) {
-    case 1: return set_attr<1>(bytes);
-    case 2: return set_attr<2>(bytes);
-    case 4: return set_attr<4>(bytes);
-    default: return set_attr<8>(bytes);
-  }
+  const cudaError_t e = set_attr<1>(bytes);
+  return e == cudaSuccess ? set_attr<8>(bytes) : e;
 }
 
 void launch_gram_solve(const Ws& ws, const CallArgs*, int B, int S, float eps, int eps_rel,
                        cudaStream_t s) {
   const size_t smem = gs_bytes(ws.N, S);
-  switch (gram_warps(ws.N)) {
-    case 1: gram_solve_kernel<1><<<B, 32, smem, s>>>(ws, B, S, eps, eps_rel); break;
-    case 2: gram_solve_kernel<2><<<B, 64, smem, s>>>(ws, B, S, eps, eps_rel); break;
-    case 4: gram_solve_kernel<4><<<B, 128, smem, s>>>(ws, B, S, eps, eps_rel); break;
-    default: gram_solve_kernel<8><<<B, 256, smem, s>>>(ws, B, S, eps, eps_rel); break;
-  }
+  if (gram_warps(ws.N, B, ws.tc_grid > 0 ? ws.tc_grid : 152) == 1)
+    gram_solve_kernel<1><<<B, 32, smem, s>>>(ws, B, S, eps, eps_rel);
+  else
+    gram_solve_kernel<8><<<B, 256, smem, s>>>(ws, B, S, eps, eps_rel);
 }
 
 }  // namespace ompk

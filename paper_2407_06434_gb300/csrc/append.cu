@@ -440,6 +440,47 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     rr += r[t].x * r[t].x + r[t].y * r[t].y + r[t].z * r[t].z + r[t].w * r[t].w;
   }
   rr = warp_sum_f(rr);
+  if (W == 1 && !top1) {
+    // The next step's quantised operand row, at this position: the compaction keeps it where
+    // no signal before this one retired, and re-quantises from R32 otherwise. Same rounding as
+    // the compaction's (BF16 round-to-nearest-even; E4M3 satfinite with the row's amax / 448).
+    const int j = (k + 1) & 1;
+    if (ws.prec == OMP_PREC_BF16) {
+      __nv_bfloat162* dq = reinterpret_cast<__nv_bfloat162*>(
+          static_cast<__nv_bfloat16*>(ws.Rq[j]) + static_cast<size_t>(p) * ws.Mp);
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int s = t * 32 + lane;
+        if (s < M4) {
+          dq[2 * s] = __floats2bfloat162_rn(r[t].x, r[t].y);
+          dq[2 * s + 1] = __floats2bfloat162_rn(r[t].z, r[t].w);
+        }
+      }
+    } else {
+      float amax = 0.f;
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int s = t * 32 + lane;
+        if (s < M4)
+          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(r[t].x), fabsf(r[t].y)), fmaxf(fabsf(r[t].z), fabsf(r[t].w))));
+      }
+      amax = warp_max(amax);
+      const float inv = amax > 0.f ? 448.f / amax : 0.f;
+      if (lane == 0) ws.sr[j][p] = amax > 0.f ? amax / 448.f : 0.f;
+      uint32_t* dq = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws.Rq[j]) + static_cast<size_t>(p) * ws.Mp);
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int s = t * 32 + lane;
+        if (s < M4) {
+          const uint32_t b0 = __nv_cvt_float_to_fp8(r[t].x * inv, __NV_SATFINITE, __NV_E4M3);
+          const uint32_t b1 = __nv_cvt_float_to_fp8(r[t].y * inv, __NV_SATFINITE, __NV_E4M3);
+          const uint32_t b2 = __nv_cvt_float_to_fp8(r[t].z * inv, __NV_SATFINITE, __NV_E4M3);
+          const uint32_t b3 = __nv_cvt_float_to_fp8(r[t].w * inv, __NV_SATFINITE, __NV_E4M3);
+          dq[s] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+        }
+      }
+    }
+  }
   if (lane == 0) gs.part[8 + wig] = rr;
   group_sync(W, grp);
   if (wig == 0 && lane == 0) {

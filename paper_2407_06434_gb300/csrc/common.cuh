@@ -193,7 +193,9 @@ void launch_gram_solve(const Ws& ws, const CallArgs* args, int B, int S, float e
 cudaError_t configure_gram_solve(const Ws& ws);
 void launch_init(const Ws& ws, const CallArgs* args, int B, cudaStream_t s);
 void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s);
-void launch_compact(const Ws& ws, int j, int B, int S, cudaStream_t s);
+// reuse: the update kernel of step j-1 has just written step j's quantised rows at the old
+// positions, so blocks whose positions do not move keep them
+void launch_compact(const Ws& ws, int j, int B, int S, bool reuse, cudaStream_t s);
 void launch_advance(const Ws& ws, int S, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_update(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
 void launch_finalize(const Ws& ws, const CallArgs* args, int B, int S, cudaStream_t s);

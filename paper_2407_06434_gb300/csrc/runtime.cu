@@ -122,7 +122,7 @@ void prof_mark(omp_handle_s* h, bool prof, int kind, int k, int end, cudaStream_
 void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStream_t s) {
   const Ws& ws = h->ws;
   launch_init(ws, h->args_dev, B, s);
-  launch_compact(ws, 0, B, S, s);
+  launch_compact(ws, 0, B, S, false, s);
   for (int k = 0; k < S; ++k) {
     prof_mark(h, prof, 0, k, 0, s);
     enqueue_correlate(h, k, B, s);
@@ -130,7 +130,7 @@ void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStre
     prof_mark(h, prof, 1, k, 0, s);
     launch_update(ws, k, B, S, eps, h->d.eps_relative, s);
     prof_mark(h, prof, 1, k, 1, s);
-    if (k + 1 < S) launch_compact(ws, k + 1, B, S, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, B, S, true, s);
   }
   launch_finalize(ws, h->args_dev, B, S, s);
 }
@@ -145,7 +145,7 @@ bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* 
   *out = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
   launch_init(ws, h->args_dev, B, s);
-  launch_compact(ws, 0, B, S, s);
+  launch_compact(ws, 0, B, S, false, s);
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -171,7 +171,7 @@ bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* 
   if (ok) {
     enqueue_correlate(h, -1, B, h->body_stream);
     launch_update(ws, -1, B, S, eps, h->d.eps_relative, h->body_stream);
-    launch_compact(ws, -1, B, S, h->body_stream);
+    launch_compact(ws, -1, B, S, true, h->body_stream);
     launch_advance(ws, S, cond, h->body_stream);
     cudaGraph_t tmp = nullptr;
     ok = cudaStreamEndCapture(h->body_stream, &tmp) == cudaSuccess;
@@ -191,7 +191,7 @@ bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* 
 
 void enqueue_topk(omp_handle_s* h, const float* R, int B, int topk, cudaStream_t s) {
   launch_load_rows(h->ws, R, B, s);
-  launch_compact(h->ws, 0, B, 1, s);
+  launch_compact(h->ws, 0, B, 1, false, s);
   enqueue_correlate(h, 0, B, s);
   launch_topk_out(h->ws, h->args_dev, B, topk, s);
 }
@@ -559,11 +559,11 @@ omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_
   if (!launch_restricted(ws, h->args_dev, cand, K, tau, b, S, eps, h->d.eps_relative, ws.fb, s))
     return OMP_ERR_CUDA;
   // signals that failed the residual-drop check continue in the dense loop
-  launch_compact(ws, 0, b, S, s);
+  launch_compact(ws, 0, b, S, false, s);
   for (int k = 0; k < S; ++k) {
     enqueue_correlate(h, k, b, s);
     launch_update(ws, k, b, S, eps, h->d.eps_relative, s);
-    if (k + 1 < S) launch_compact(ws, k + 1, b, S, s);
+    if (k + 1 < S) launch_compact(ws, k + 1, b, S, true, s);
   }
   launch_finalize(ws, h->args_dev, b, S, s);
   return check_launch();

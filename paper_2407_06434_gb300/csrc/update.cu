@@ -81,7 +81,7 @@ void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s) {
 // sr[j&1]); one warp per row, the row's loads issued together in batches of 8 per lane.
 constexpr int kCompactChunk = 16;
 
-__global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
+__global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int reuse) {
   j = j >= 0 ? j : *ws.kdev + 1;  // -1: the step after the loop's current iteration
   if (j >= S) return;           // no further iteration reads this list
   __shared__ int dest_s[kCompactChunk];
@@ -121,6 +121,13 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
     ws.cnt[j + 1] = before + total;
   }
   const int M4 = ws.Mp / 4;
+  // Positions that do not move (nothing before them retired) keep the quantised rows the
+  // one-warp update kernel wrote for them; other blocks quantise from the FP32 residuals.
+  int keep_all = 1;
+  for (int i = 0; i < kCompactChunk; ++i)
+    if (p0 + i < Lin && dest_s[i] != i) keep_all = 0;
+  const bool rows_in_place = reuse && ws.upd_w == 1 && ws.prec != OMP_PREC_FP32 && before == p0 &&
+                             keep_all;
   for (int i = warp; i < kCompactChunk; i += 8) {
     const int r = dest_s[i];
     if (r < 0) continue;
@@ -130,6 +137,7 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
       out[dest] = id;
       ws.cand1[dest] = 0ull;
     }
+    if (rows_in_place) continue;
     const float4* src = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
@@ -191,8 +199,8 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S) {
   }
 }
 
-void launch_compact(const Ws& ws, int j, int B, int S, cudaStream_t s) {
-  compact_kernel<<<(B + kCompactChunk - 1) / kCompactChunk, 256, 0, s>>>(ws, j, S);
+void launch_compact(const Ws& ws, int j, int B, int S, bool reuse, cudaStream_t s) {
+  compact_kernel<<<(B + kCompactChunk - 1) / kCompactChunk, 256, 0, s>>>(ws, j, S, reuse ? 1 : 0);
 }
 
 // End of one pass of the graph's while loop: advance the iteration counter and keep looping

@@ -1,22 +1,23 @@
-// Per-iteration selection, inverse-Cholesky append and residual update, one group of W warps
-// per live signal (W = 1 for padded lengths up to 1024, up to 8 for 8192).
+// Per-iteration selection, inverse-Cholesky append and residual update, one block of W warps
+// per live signal (W = 1 for padded lengths up to 1024, up to 8 for 8192; the autotuner picks).
 //
 // Iteration k (0-based; the paper's k+1), following Sec. 2.3:
-//   n*    the correlation's pick (FP32 path) or the best of its top-8 rescored in FP32
+//   n*    the correlation's pick (FP32 path), or the best of the merged top-8 rescored in FP32
+//         (quantised paths; skipped when a rigorous error bound shows the quantised best wins)
 //   w     = A_S^T a_{n*}          read from the Gram matrix row n* (Sec. 2.2 precompute)
-//   z     = F_k^T w               FP64
-//   delta = ||a_{n*}||^2 - ||z||^2; the atom is dependent if delta <= 1e-10 ||a_{n*}||^2
+//   z     = F_k^T w               FP32, on an FP32 copy of F staged in shared memory
+//   delta = ||a_{n*}||^2 - ||z||^2 in FP64; the atom is dependent if delta <= 1e-10 ||a_{n*}||^2
 //   gamma = 1 / sqrt(delta)       FP64: the diagonal of the new inverse-Cholesky column
-//   F[:,k] = [-gamma F_k z ; gamma]
+//   F[:,k] = [-gamma F_k z ; gamma]  (stored in FP64 and FP32)
 //   q     = A_{S+n*} F[:,k]       the new orthonormal direction (FP32 gather of k+1 atom rows)
 //   b_k   = q^T r,  r <- r - b_k q (y_hat = A_k F_k (A_k F_k)^T y built one term at a time)
+// and, with one warp per signal, the next step's quantised operand row at this position.
 //
-// Layout of the work: the residual and q live in registers, sliced over the group's lanes in
+// Layout of the work: the residual and q live in registers, sliced over the block's lanes in
 // float4 slots (slot s of a row belongs to lane s mod 32 of warp (s / 32) mod W). The small
-// triangular work runs in the group's first warp, lane-parallel over rows or columns of F.
-// GB300 issues FP64 at a small fraction of its FP32 rate, so only the Schur complement, gamma
-// and the stored factor are FP64; z and F z use an FP32 copy of F. Group members meet only at
-// group-scoped named barriers.
+// triangular work runs in the first warp, lane-parallel over rows or columns of F. GB300 issues
+// FP64 at a small fraction of its FP32 rate, so only the Schur complement, gamma and the stored
+// factor are FP64; their FP32 inputs (w from the FP32 Gram matrix) carry no more precision.
 #include "common.cuh"
 
 namespace ompk {

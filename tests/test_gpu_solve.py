@@ -3,7 +3,8 @@
 Sizes: the hand-worked fixtures; the 64 x 256 planted workload in full; ragged shapes that span
 several correlation tiles with a partial last tile in M, N and B; eps-stopped uneven batches;
 the full-size 1024 x 8192, B = 4096, S = 32 workload checked on sampled signals; edge cases
-(zero and non-finite signals, dependent atoms, exact ties across tiles)."""
+(zero and non-finite signals, dependent atoms, exact ties across tiles, a single signal, a
+128-step support, the largest signal length, scale equivariance over 24 orders of magnitude)."""
 import numpy as np
 import pytest
 
@@ -368,3 +369,46 @@ def test_read_bandwidth_probe():
     assert omp.load().omp_read_bandwidth_probe(buf.data_ptr(), 12, 1, out.data_ptr(), 64, None) != 0
     gbs = omp.read_bandwidth_gbs(32, 10)
     assert np.isfinite(gbs) and gbs > 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_signal_and_long_support(prec):
+    """B = 1 (one partial tile everywhere) and a long run, S = 128 on a 256 x 512 dictionary."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=512, B=1, S=128, s_min=100, s_max=100,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=13)
+    Y, *_ = gen.signals(w, A, seed=13)
+    ref = oracle.omp_batch(A, Y, w.S)
+    r = solve(prec, A, Y, w.S)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"])
+    assert st["tie_diverged"] == 0, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_longest_signal_length(prec):
+    """M = 8192, the largest padded length (eight warps per signal in the update, 64 or 128
+    tensor-core K stages per unit), with a ragged atom count and batch."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=8192, N=700, B=70, S=12, s_min=4, s_max=12,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=14)
+    Y, *_ = gen.signals(w, A, seed=14)
+    ref = oracle.omp_batch(A, Y, w.S)
+    r = solve(prec, A, Y, w.S)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"])
+    assert st["tie_diverged"] <= 1, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_scale_equivariance(prec, scale):
+    """OMP is scale-equivariant in y (App. A): scaling the batch by 1e-12 or 1e12 picks the same
+    supports, scales the coefficients by the same factor and keeps the relative eps stop."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=128, N=512, B=40, S=16, s_min=4, s_max=12,
+                       sigma=1e-6, col_scale=1.0)
+    A = gen.dictionary(w, seed=15)
+    Y, *_ = gen.signals(w, A, seed=15)
+    r1 = solve(prec, A, Y, w.S, eps=1e-3)
+    r2 = solve(prec, A, (Y * scale).astype(np.float32), w.S, eps=1e-3)
+    assert np.array_equal(r1["sup"], r2["sup"])
+    assert np.array_equal(r1["n_iter"], r2["n_iter"])
+    np.testing.assert_allclose(r2["X"], r1["X"] * scale, rtol=1e-4, atol=1e-6 * scale)

@@ -43,6 +43,23 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// 16-byte global -> shared copy (L2 only) that holds no register while in flight
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+
 struct GroupSmem {
   float* w;      // Smax: A_S^T a_{n*} (Gram row entries)
   float* z;      // Smax: F^T w
@@ -53,6 +70,8 @@ struct GroupSmem {
   double* part;  // 16: per-warp partials of b and ||r||^2
   int* scal;     // 4: n*, dependent flag, rescoring skipped
   float* top2;   // 2: the merged lists' best and second-best quantised scores
+  float* rinv;   // 2: inverse norms of the two best merged candidates (threshold on)
+  float* rows;   // 2 x Mp when the threshold is on: FP32 rows of the two best merged candidates
   float* tri;    // Smax (Smax + 1) / 2 when Smax <= kTriMax: staged copy of the packed FP32 F
 };
 
@@ -60,17 +79,27 @@ __host__ __device__ __forceinline__ size_t tri_floats(int Smax) {
   return Smax <= kTriMax ? static_cast<size_t>(Smax) * (Smax + 1) / 2 : 0;
 }
 
-__host__ __device__ __forceinline__ size_t group_bytes(int Smax) {
+// rows of the two best merged candidates, staged for the next step's threshold
+__host__ __device__ __forceinline__ size_t row_floats(const Ws& ws) {
+  return ws.tau ? 2 * static_cast<size_t>(ws.Mp) : 0;
+}
+
+__host__ __device__ __forceinline__ size_t group_bytes(const Ws& ws) {
+  const int Smax = ws.Smax;
   const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
-                   8 * 4 + 16 * 8 + 16 + 8 + (tri_floats(Smax) * 4 + 15) / 16 * 16;
+                   8 * 4 + 16 * 8 + 16 + 8 + 8 + row_floats(ws) * 4 +
+                   (tri_floats(Smax) * 4 + 15) / 16 * 16;
   return (b + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, int Smax) {
-  unsigned char* g = base + grp * group_bytes(Smax);
+__device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, const Ws& ws) {
+  const int Smax = ws.Smax;
+  unsigned char* g = base + grp * group_bytes(ws);
   GroupSmem s;
   s.tri = reinterpret_cast<float*>(g);  // first, so it is 16-byte aligned
   g += (tri_floats(Smax) * 4 + 15) / 16 * 16;
+  s.rows = reinterpret_cast<float*>(g);  // 16-byte aligned too
+  g += row_floats(ws) * 4;
   s.part = reinterpret_cast<double*>(g);
   s.f = reinterpret_cast<float*>(g + 16 * 8);
   s.sup = reinterpret_cast<int*>(s.f + Smax + 1);
@@ -80,6 +109,7 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, in
   s.w = reinterpret_cast<float*>(s.scal + 4);
   s.z = s.w + Smax;
   s.top2 = s.z + Smax;
+  s.rinv = s.top2 + 2;
   return s;
 }
 
@@ -165,7 +195,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   const int id = ws.live[k & 1][p];
   const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
   extern __shared__ __align__(16) unsigned char smem[];
-  GroupSmem gs = group_smem(smem, grp, ws.Smax);
+  GroupSmem gs = group_smem(smem, grp, ws);
 
   // The candidate lists head the critical path (merge, rescoring, append), so their loads are
   // issued first; they are only read at the merge below.
@@ -202,6 +232,8 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   }
   const float rprev = ws.rnorm[id];
   const float ynorm = ws.ynorm[id];
+  // the pruning threshold the correlation used for this position (0: none)
+  const float tau_used = ws.tau_pos ? ws.tau_pos[p] : 0.f;
 
   const int M4 = ws.Mp >> 2;
   const float4* rrow = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
@@ -259,15 +291,35 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       // The rescoring can only confirm the quantised best when its lead over the second is
       // more than twice the bound on |quantised - FP32| score (rescore_eps ||r||, from the
       // quantisation and both accumulations, with ||a|| inv_norm = 1): every other candidate's
-      // FP32 score is then strictly below the best one's, so the rescoring is skipped.
+      // FP32 score is then strictly below the best one's, so the rescoring is skipped. Columns
+      // that the correlation pruned scored at most tau_used, so tau_used stands in for a
+      // missing second.
       if (lane == 0) {
-        const float lead = gs.top2[0] - gs.top2[1];
+        const float lead = gs.top2[0] - fmaxf(gs.top2[1], tau_used);
         gs.scal[2] = (ws.rescore_eps > 0.f && rprev > 1e-30f && gs.cidx[0] >= 0 &&
                       lead > 2.f * ws.rescore_eps * rprev) ? 1 : 0;
       }
     }
     group_sync(W, grp);
     const bool skip = gs.scal[2] != 0;
+    if (ws.tau) {
+      // the two best merged candidates' FP32 rows and inverse norms, for the next step's
+      // threshold: copied to shared memory in the background (each warp its own slots), read at
+      // the end of the kernel
+      for (int c = 0; c < 2 && c < ws.topk; ++c) {
+        const int n = gs.cidx[c];
+        if (n < 0) continue;
+        const float4* src = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n) * ws.Mp);
+        float4* dst = reinterpret_cast<float4*>(gs.rows + static_cast<size_t>(c) * ws.Mp);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          const int s = t * (W * 32) + wig * 32 + lane;
+          if (s < M4) cp_async16(dst + s, src + s);
+        }
+        if (wig == 0 && lane == c) cp_async4(gs.rinv + c, ws.inv_norm + n);
+      }
+      cp_async_commit();
+    }
     // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
     // candidates per pass so their row loads are in flight together
     for (int c = 0; !skip && c < ws.topk; c += 2) {
@@ -346,6 +398,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   }
   group_sync(W, grp);
   if (gs.scal[1]) {
+    if (ws.tau) cp_async_wait_all();  // no copy outlives the block
     if (wig == 0 && lane == 0) {
       ws.flag[p] = 0;
       ws.stop[id] = kStopDependent;
@@ -441,6 +494,29 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     rr += r[t].x * r[t].x + r[t].y * r[t].y + r[t].z * r[t].z + r[t].w * r[t].w;
   }
   rr = warp_sum_f(rr);
+  if (ws.tau) {
+    // this warp's part of a_c^T r_k for the two staged candidate rows
+    cp_async_wait_all();
+    __syncwarp();
+    const float4* x0 = reinterpret_cast<const float4*>(gs.rows);
+    const float4* x1 = reinterpret_cast<const float4*>(gs.rows + ws.Mp);
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int s = t * (W * 32) + wig * 32 + lane;
+      if (s < M4) {
+        const float4 u0 = x0[s], u1 = x1[s];
+        d0 += u0.x * r[t].x + u0.y * r[t].y + u0.z * r[t].z + u0.w * r[t].w;
+        d1 += u1.x * r[t].x + u1.y * r[t].y + u1.z * r[t].z + u1.w * r[t].w;
+      }
+    }
+    d0 = warp_sum_f(d0);
+    d1 = warp_sum_f(d1);
+    if (lane == 0) {
+      gs.cpart[2 * wig] = d0;
+      gs.cpart[2 * wig + 1] = d1;
+    }
+  }
   if (W == 1 && !top1) {
     // The next step's quantised operand row, at this position: the compaction keeps it where
     // no signal before this one retired, and re-quantises from R32 otherwise. Same rounding as
@@ -507,12 +583,37 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     }
     ws.flag[p] = static_cast<uint8_t>(cont);
   }
+
+  // ---------------------------------------------------------------- next step's threshold
+  // BF16 path with the rescoring bound. The exact FP32 correlation of the new residual with a
+  // runner-up candidate m of this step (one of the two best merged ones, not the pick), less
+  // its rounding bound Mp 2^-23 ||r_k||, is a lower bound L on the next residual's best score.
+  // A column whose quantised score is at most L - 3 rescore_eps ||r_k|| has an FP32 score more
+  // than 2 rescore_eps ||r_k|| below the best, so it can be neither the pick nor a rescoring
+  // candidate that changes it: the next correlation drops such columns before its top-8
+  // insertion.
+  if (ws.tau && wig == 0 && lane == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
+    const float rk = static_cast<float>(sqrt(tot));
+    float best = 0.f;
+    for (int c = 0; c < 2 && c < ws.topk; ++c) {
+      const int n = gs.cidx[c];
+      if (n < 0 || n == ns) continue;
+      float d = 0.f;
+      for (int w = 0; w < W; ++w) d += gs.cpart[2 * w + c];
+      best = fmaxf(best, fabsf(d) * gs.rinv[c]);
+    }
+    const float lb = best * (1.f - 0x1p-20f) - static_cast<float>(ws.Mp) * 0x1p-23f * rk;
+    const float tau = lb - 3.f * ws.rescore_eps * rk;
+    ws.tau[id] = TauRec{tau > 0.f ? tau : 0.f, k + 1};
+  }
 }
 
 // W warps per signal and V float4 slots per lane cover Mp <= 128 W V.
 template <int W, int V>
 void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  const size_t smem = group_bytes(ws.Smax);
+  const size_t smem = group_bytes(ws);
   append_update_kernel<W, V><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
 }
 
@@ -532,7 +633,7 @@ cudaError_t set_attr_t(int bytes) {
 
 template <int W>
 cudaError_t set_attr_w(const Ws& ws) {
-  const int bytes = static_cast<int>(group_bytes(ws.Smax));
+  const int bytes = static_cast<int>(group_bytes(ws));
   cudaError_t e = set_attr_t<W, 1>(bytes);
   if (e == cudaSuccess) e = set_attr_t<W, 2>(bytes);
   if (e == cudaSuccess) e = set_attr_t<W, 4>(bytes);

@@ -35,10 +35,17 @@ namespace ompk {
 constexpr int kMpAlign = 64;          // M padding (x2 for E4M3): one 128-byte K stage
 constexpr int kSigTile = 128;         // signals per correlation tile (TMEM lanes)
 constexpr int kMaxTopk = 8;
+constexpr int kTauSmax = 64;          // the BF16 pruning threshold is kept for max_iters <= 64
 constexpr int kPieces = 32;           // candidate slots per position (quantised paths)
 constexpr int kTcParts = 2;           // candidate lists per signal and correlation CTA
 constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a||^2
 constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
+
+// BF16 path: a signal's pruning threshold for the correlation of step `step` (see append.cu)
+struct alignas(8) TauRec {
+  float tau;
+  int step;
+};
 
 struct Ws {
   int M, Mp, N, Smax, Bmax, Bpad;
@@ -68,6 +75,8 @@ struct Ws {
   int* cnt;
   int* kdev;       // iteration counter of the graph's device-side loop
   float rescore_eps;  // bound on |quantised score - FP32 score| per unit of ||r|| (0: none)
+  TauRec* tau;     // BF16 with the rescoring bound: per signal, next step's pruning threshold
+  float* tau_pos;  // the same per live position of the current step (0: no pruning); or null
   uint8_t* flag;
   unsigned long long* cand1;
   float* cand_s;

@@ -13,6 +13,11 @@
 // keeps its own list; a CTA flushes them for signal tile s into candidate slots
 // EPI_PARTS (g - owner(s * Tn)) + part, so a tile's lists occupy consecutive slots; the
 // mainloop's minimum units per CTA (`cmin`) bounds the pieces per tile by kPieces / EPI_PARTS.
+//
+// On the BF16 path each row may carry a pruning threshold from the previous step's update (a
+// lower bound on its best score less three score error bounds, see append.cu): columns at or
+// below it are not inserted, which removes most of the insertion work once the solve is past
+// its first step.
 #include "tcgemm.cuh"
 
 namespace ompk {
@@ -81,6 +86,9 @@ struct EpiTop8 {
   unsigned long long* peers;
   float4 pf;  // prefetched scales of column tile pf_t (this lane's 4 of the warp's 128)
   int pf_t;
+  float thr0;    // this row's pruning threshold in the current signal tile (-1: none)
+  float pf_tau;  // the row's threshold in signal tile pf_tau_s, loaded ahead
+  int pf_tau_s;
 
   __device__ void reset() {
 #pragma unroll
@@ -101,6 +109,15 @@ struct EpiTop8 {
       ws.cand_i[off + q] = ti[q];
     }
   }
+  // The update kernel's lower bound on the row's best score, less three score error bounds
+  // (written per live position by the compaction); a column at or below it can be neither the
+  // pick nor a rescoring candidate that changes it. BF16 path only.
+  __device__ float load_tau(int s) const {
+    const int p = s * BM + row;
+    if (!ws.tau_pos || p >= L) return -1.f;
+    const float v = __ldg(ws.tau_pos + p);
+    return v > 0.f ? v : -1.f;
+  }
   // this lane's EPI_COLS / 32 consecutive scales of the warp's columns of tile t
   __device__ float4 load_scales(int t) const {
     static_assert(EPI_COLS == 128, "one float4 per lane");
@@ -117,6 +134,8 @@ struct EpiTop8 {
     row = row_;
     part = part_;
     cur_s = -1;
+    thr0 = -1.f;
+    pf_tau_s = -1;
     reset();
   }
   __device__ void unit(int s, int t) {
@@ -124,6 +143,9 @@ struct EpiTop8 {
       if (cur_s >= 0) flush(cur_s);
       cur_s = s;
       reset();
+      thr0 = pf_tau_s == s ? pf_tau : load_tau(s);
+      pf_tau_s = s + 1;  // the next signal tile of this CTA's range, if any
+      pf_tau = load_tau(s + 1);
     }
     const float4 v = pf_t == t ? pf : load_scales(t);
     __syncwarp();  // every lane has finished with the previous unit's scales
@@ -138,14 +160,15 @@ struct EpiTop8 {
   // is seeded, without a per-column loop, with the best column of each group of 4 (lowest index
   // on ties): those 8 are distinct columns of the chunk, so their smallest score is a safe
   // threshold for the rest (at least 8 scores reach it), and a high one, which keeps the first
-  // chunk's insertions few.
+  // chunk's insertions few. A row with a pruning threshold is not seeded: its threshold already
+  // holds back all but the few columns near the best, so its list may stay short of 8.
   __device__ void chunk(int, int t, int c0, const uint32_t (&cur)[32]) {
     const int nb = t * BN + c0;
     const int lim = min(32, ws.N - nb);
     const float* scl = scr + (c0 - part * EPI_COLS);
     const float4* sc4 = reinterpret_cast<const float4*>(scl);
     uint32_t seeded = 0;
-    if (ti[0] < 0) {
+    if (ti[0] < 0 && thr0 < 0.f) {
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         float bv = -1.f;
@@ -167,7 +190,7 @@ struct EpiTop8 {
     }
     // own 8th best, raised to just below each other part's when that one is positive and
     // belongs to the same signal tile (x >= other  <=>  x > its predecessor, for x >= 0)
-    float thr = ts[7];
+    float thr = fmaxf(ts[7], thr0);
 #pragma unroll
     for (int o = 1; o < EPI_PARTS; ++o) {
       const int q = (part + o) % EPI_PARTS;

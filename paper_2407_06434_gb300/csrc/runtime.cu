@@ -368,6 +368,8 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
     ok = ok && dalloc(h, &ws.cand_s, Bp * ws.pieces * kMaxTopk) &&
          dalloc(h, &ws.cand_i, Bp * ws.pieces * kMaxTopk);
   }
+  if (ws.prec == OMP_PREC_BF16 && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
+    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp);
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
@@ -386,6 +388,8 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   bool cuda_ok = cudaMemset(ws.err, 0, sizeof(unsigned)) == cudaSuccess &&
                  (!ws.escale || cudaMemset(ws.escale, 0, Npad * sizeof(float)) == cudaSuccess) &&
                  cudaMemset(ws.cand1, 0, Bm * sizeof(unsigned long long)) == cudaSuccess &&
+                 (!ws.tau || cudaMemset(ws.tau, 0xff, Bm * sizeof(TauRec)) == cudaSuccess) &&
+                 (!ws.tau_pos || cudaMemset(ws.tau_pos, 0, Bp * sizeof(float)) == cudaSuccess) &&
                  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  configure_update_kernels(ws) == cudaSuccess;

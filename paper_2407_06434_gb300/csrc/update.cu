@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, 
     ws.flag[b] = alive ? 1 : 0;
     ws.fb[b] = -1;
     ws.live[1][b] = b;
+    if (ws.tau) ws.tau[b] = TauRec{0.f, -1};
     if (!finite) atomicOr(ws.err, OMP_DEVERR_NONFINITE);
     if (b == 0) ws.cnt[0] = B;
   }
@@ -136,6 +137,10 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (lane == 0) {
       out[dest] = id;
       ws.cand1[dest] = 0ull;
+      if (ws.tau_pos) {  // the update kernel of step j - 1 wrote this signal's threshold
+        const TauRec t = j > 0 ? ws.tau[id] : TauRec{0.f, -1};
+        ws.tau_pos[dest] = t.step == j && t.tau > 0.f ? t.tau : 0.f;
+      }
     }
     if (rows_in_place) continue;
     const float4* src = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);

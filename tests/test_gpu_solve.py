@@ -191,15 +191,35 @@ def test_device_loop_stops_when_no_signal_is_live(prec):
     assert passes == int(ng.max()) and passes < w.S
 
 
-def test_rescoring_shortcut_is_exact(monkeypatch):
+SHORTCUT_CASES = {
+    # many close calls: coherent pairs among the planted atoms, noise-level late steps
+    "noisy_256x2048": ("gaussian_64x256_s8_b16",
+                       dict(M=256, N=2048, B=512, S=48, s_min=8, s_max=40, sigma=1e-2,
+                            col_scale=1.0), 11),
+    # the benchmark shape, whole batch
+    "bench_1024x8192": ("gaussian_1024x8192_s32_b4096", {}, 0),
+    # paired atoms at correlation ~0.3 with unequal column norms: the Gram terms of the
+    # threshold bound are large
+    "coherent_512x4096": ("coherent_4096x32768_s64_b16384",
+                          dict(M=512, N=4096, B=1024, S=40, s_min=40, s_max=40), 5),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SHORTCUT_CASES))
+def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case):
     """BF16 skips the FP32 rescoring when the quantised best leads the second by more than twice
-    the quantisation error bound; the supports and coefficients must be bit-identical to always
-    rescoring, on a workload with many close calls (coherent pairs, noise-level late steps)."""
+    the quantisation error bound, and its correlation drops columns below the pruning threshold
+    that the previous step's update derived from its runner-up candidates. Neither may change a
+    pick: the supports, coefficients and residual norms must be bit-identical to always
+    rescoring with no pruning (OMP_RESCORE_ALWAYS=1 turns both off)."""
     from paper_2407_06434_gb300 import omp
-    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=2048, B=512, S=48, s_min=8, s_max=40,
-                       sigma=1e-2, col_scale=1.0)
-    A = gen.dictionary(w, seed=11)
-    Y, *_ = gen.signals(w, A, seed=11)
+    name, over, seed = SHORTCUT_CASES[case]
+    w = gen.get_config(name, **over)
+    A = gen.dictionary(w, seed=seed)
+    if w.dict_kind == "coherent":
+        scale = np.random.default_rng(seed).uniform(0.5, 2.0, w.N).astype(np.float32)
+        A = np.asfortranarray(A * scale[None, :])
+    Y, *_ = gen.signals(w, A, seed=seed)
     Ad = dev_dict(A)
     Yd = torch.from_numpy(Y).cuda()
     out = {}
@@ -209,6 +229,7 @@ def test_rescoring_shortcut_is_exact(monkeypatch):
         X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, 0.0, diagnostics=True)
         torch.cuda.synchronize()
         out[always] = (X.cpu().numpy(), sup.cpu().numpy(), resid.cpu().numpy())
+        assert omp.omp_get_error(s.h)[1] == 0
         s.close()
     assert np.array_equal(out["0"][1], out["1"][1])
     assert np.array_equal(out["0"][0].view(np.uint32), out["1"][0].view(np.uint32))

@@ -68,7 +68,7 @@ struct GroupSmem {
   float* cpart;  // 8 x 8: rescoring partial dot products [candidate][warp]
   int* cidx;     // 8
   double* part;  // 16: per-warp partials of b and ||r||^2
-  int* scal;     // 4: n*, dependent flag, rescoring skipped
+  int* scal;     // 4: n*, dependent flag, rescoring skipped, candidates to rescore
   float* top2;   // 2: the merged lists' best and second-best quantised scores
   float* rinv;   // 2: inverse norms of the two best merged candidates (threshold on)
   float* rows;   // 2 x Mp when the threshold is on: FP32 rows of the two best merged candidates
@@ -256,6 +256,12 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
           vs[t] = -1.f;
           vi[t] = 0x7fffffff;
         }
+      // Candidates come out best first; one more than 2 rescore_eps ||r|| below the best has an
+      // FP32 score strictly below the best one's, so the rescoring stops before it.
+      const bool bound = ws.rescore_eps > 0.f && rprev > 1e-30f;
+      const float win = 2.f * ws.rescore_eps * rprev;
+      float s_first = 0.f;
+      int nres = ws.topk;
       for (int sel = 0; sel < ws.topk; ++sel) {
         float bs = -2.f;
         int bi = 0x7fffffff, bt = -1;
@@ -287,7 +293,12 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         }
         if (lane == 0) gs.cidx[sel] = (g_i >= 0 && g_i < ws.N) ? g_i : -1;
         if (lane == 0 && sel < 2) gs.top2[sel] = g_s;
+        if (sel == 0)
+          s_first = g_s;
+        else if (bound && nres == ws.topk && !(g_s >= s_first - win))
+          nres = sel;
       }
+      if (lane == 0) gs.scal[3] = nres;
       // The rescoring can only confirm the quantised best when its lead over the second is
       // more than twice the bound on |quantised - FP32| score (rescore_eps ||r||, from the
       // quantisation and both accumulations, with ||a|| inv_norm = 1): every other candidate's
@@ -302,6 +313,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     }
     group_sync(W, grp);
     const bool skip = gs.scal[2] != 0;
+    const int nres = gs.scal[3];
     if (ws.tau) {
       // the two best merged candidates' FP32 rows and inverse norms, for the next step's
       // threshold: copied to shared memory in the background (each warp its own slots), read at
@@ -322,9 +334,9 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     }
     // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
     // candidates per pass so their row loads are in flight together
-    for (int c = 0; !skip && c < ws.topk; c += 2) {
+    for (int c = 0; !skip && c < nres; c += 2) {
       const int n0 = gs.cidx[c];
-      const int n1 = c + 1 < ws.topk ? gs.cidx[c + 1] : -1;
+      const int n1 = c + 1 < nres ? gs.cidx[c + 1] : -1;
       const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n0 < 0 ? 0 : n0) * ws.Mp);
       const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n1 < 0 ? 0 : n1) * ws.Mp);
       float acc0 = 0.f, acc1 = 0.f;
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       acc1 = warp_sum_f(acc1);
       if (lane == 0) {
         gs.cpart[c * 8 + wig] = acc0;
-        if (c + 1 < ws.topk) gs.cpart[(c + 1) * 8 + wig] = acc1;
+        if (c + 1 < nres) gs.cpart[(c + 1) * 8 + wig] = acc1;
       }
     }
     group_sync(W, grp);
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     } else if (wig == 0) {
       float sc = -2.f;
       int ix = 0x7fffffff;
-      if (lane < ws.topk && gs.cidx[lane] >= 0) {
+      if (lane < nres && gs.cidx[lane] >= 0) {
         float v = 0.f;
         for (int w = 0; w < W; ++w) v += gs.cpart[lane * 8 + w];
         ix = gs.cidx[lane];

@@ -76,7 +76,13 @@ using namespace tcg;
 // are then no longer each part's own top 8, but their union still holds the row's top 8, which
 // is all the merge downstream needs. A stale value (the slots are read without a barrier) is
 // smaller and only prunes less; a value tagged with another tile is ignored.
+template <int PREC>
 struct EpiTop8 {
+  // BF16 rows may be pruned by a threshold; each list then also keeps its running best column
+  // as a key (score bits with the low 5 mantissa bits replaced by 31 - the column's place in its
+  // chunk, so that an integer max takes the higher score and, within 2^-18, the lower index) and
+  // emits it if nothing passed the threshold, so the merged lists always offer a runner-up
+  static constexpr bool kTrack = PREC == OMP_PREC_BF16;
   Ws ws;
   int L;
   int g, T, Geff, row, part, cur_s;
@@ -86,6 +92,8 @@ struct EpiTop8 {
   unsigned long long* peers;
   float4 pf;  // prefetched scales of column tile pf_t (this lane's 4 of the warp's 128)
   int pf_t;
+  uint32_t lbk;  // running best key of the list (kTrack) and its column
+  int lbi;
   float thr0;    // this row's pruning threshold in the current signal tile (-1: none)
   float pf_tau;  // the row's threshold in signal tile pf_tau_s, loaded ahead
   int pf_tau_s;
@@ -96,10 +104,18 @@ struct EpiTop8 {
       ts[q] = -1.f;
       ti[q] = -1;
     }
+    lbk = 0;
+    lbi = -1;
   }
   __device__ void flush(int s) {
     const int p = s * BM + row;
     if (p >= L) return;
+    if (kTrack && ti[0] < 0 && lbi >= 0) {
+      // nothing passed the threshold: the list's best column, its score rounded up (the
+      // rescoring shortcut reads list scores as upper bounds of the second best)
+      ts[0] = __uint_as_float(lbk | 31u);
+      ti[0] = lbi;
+    }
     const int piece = g - tc_owner(s * ws.tc_tn, T, Geff);
     const size_t off =
         (static_cast<size_t>(p) * ws.pieces + EPI_PARTS * piece + part) * kMaxTopk;
@@ -199,14 +215,25 @@ struct EpiTop8 {
       if (static_cast<int>(v >> 32) == cur_s && othr > 0.f)
         thr = fmaxf(thr, __uint_as_float(__float_as_uint(othr) - 1u));
     }
-    uint32_t mask = 0;
+    uint32_t mask = 0, kmax = 0;
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
       const float4 sc = sc4[j4];
-      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x > thr ? 1u : 0u) << (4 * j4 + 0);
-      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y > thr ? 1u : 0u) << (4 * j4 + 1);
-      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z > thr ? 1u : 0u) << (4 * j4 + 2);
-      mask |= (fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w > thr ? 1u : 0u) << (4 * j4 + 3);
+      const float v[4] = {fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x,
+                          fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y,
+                          fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z,
+                          fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = 4 * j4 + q;
+        mask |= (v[q] > thr ? 1u : 0u) << j;
+        // columns past N score 0 (zero escale), so they never beat a real column's key
+        if (kTrack) kmax = max(kmax, (__float_as_uint(v[q]) & ~31u) | static_cast<uint32_t>(31 - j));
+      }
+    }
+    if (kTrack && (kmax & ~31u) > (lbk & ~31u)) {  // strictly higher: an earlier column keeps a tie
+      lbk = kmax;
+      lbi = nb + 31 - static_cast<int>(kmax & 31u);
     }
     if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
     mask &= ~seeded;
@@ -231,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   k = iter_of(ws, k);
   const int L = ws.cnt[k + 1];
   if (L <= 0) return;
-  EpiTop8 epi;
+  EpiTop8<PREC> epi;
   epi.ws = ws;
   epi.L = L;
   const int row_tiles = (L + BM - 1) / BM;

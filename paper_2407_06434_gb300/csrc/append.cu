@@ -297,6 +297,11 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
           s_first = g_s;
         else if (bound && nres == ws.topk && !(g_s >= s_first - win))
           nres = sel;
+        if (nres < ws.topk) {  // the window is closed and the two best are known
+          if (lane == 0)
+            for (int c = sel + 1; c < ws.topk; ++c) gs.cidx[c] = -1;
+          break;
+        }
       }
       if (lane == 0) gs.scal[3] = nres;
       // The rescoring can only confirm the quantised best when its lead over the second is

@@ -644,8 +644,7 @@ void launch_w(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, 
 
 template <int W, int V>
 cudaError_t set_attr_t(int bytes) {
-  return cudaFuncSetAttribute(append_update_kernel<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  return raise_smem_limit(reinterpret_cast<const void*>(append_update_kernel<W, V>), bytes);
 }
 
 template <int W>

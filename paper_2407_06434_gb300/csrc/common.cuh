@@ -192,6 +192,11 @@ __device__ __forceinline__ int tc_piece_count(const Ws& ws, int L, int p) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// A kernel's dynamic shared memory limit is one setting of the process, shared by every handle,
+// so it is only ever raised: handles with smaller layouts leave a larger one's limit in place.
+// Thread-safe (update.cu).
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+
 // Host-side launchers (defined in the .cu files).
 void launch_prep(const Ws& ws, const float* A, cudaStream_t s);
 void launch_gram_simt(const Ws& ws, cudaStream_t s);

@@ -328,8 +328,7 @@ int gram_warps(int N, int B, int sms) { return (N <= 1536 && B >= 2 * 16 * sms) 
 
 template <int W>
 cudaError_t set_attr(size_t bytes) {
-  return cudaFuncSetAttribute(gram_solve_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(bytes));
+  return raise_smem_limit(reinterpret_cast<const void*>(gram_solve_kernel<W>), bytes);
 }
 
 }  // namespace

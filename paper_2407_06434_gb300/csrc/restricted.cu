@@ -253,9 +253,7 @@ bool launch_restricted(const Ws& ws, const CallArgs* args, const int* cand, int 
   if (per_cta < 1) return false;
   if (per_cta > 8) per_cta = 8;
   const size_t smem = per * per_cta;
-  if (cudaFuncSetAttribute(restricted_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
-    return false;
+  if (raise_smem_limit(reinterpret_cast<const void*>(restricted_kernel), smem) != cudaSuccess) return false;
   restricted_kernel<<<(B + per_cta - 1) / per_cta, 32 * per_cta, smem, s>>>(ws, args, cand, K, tau, B, S, eps,
                                                                              eps_rel, fallback);
   return cudaGetLastError() == cudaSuccess;

@@ -1,9 +1,21 @@
 // Per-signal kernels around the OMP iteration: initialisation, live-set compaction, the final
 // back-substitution x = F b (FP64), and the top-k output of omp_correlate_topk. The per-iteration
 // append and residual update is in append.cu.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ompk {
+
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
 
 // ------------------------------------------------------------------------------------ args
 __global__ void set_args_kernel(CallArgs* dst, CallArgs v) { *dst = v; }

@@ -433,3 +433,36 @@ def test_scale_equivariance(prec, scale):
     assert np.array_equal(r1["sup"], r2["sup"])
     assert np.array_equal(r1["n_iter"], r2["n_iter"])
     np.testing.assert_allclose(r2["X"], r1["X"] * scale, rtol=1e-4, atol=1e-6 * scale)
+
+
+def test_handles_with_different_layouts_coexist():
+    """A kernel's shared-memory limit is one setting of the process: a handle whose layout is
+    smaller (FP32, or fewer iterations, or a smaller dictionary for the Gram-space form) must
+    not lower the limit under a handle created before it."""
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=2048, B=300, S=48, s_min=8, s_max=40,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=2)
+    Y, *_ = gen.signals(w, A, seed=2)
+    Ad = dev_dict(A)
+    Yd = torch.from_numpy(Y).cuda()
+    big = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+    X0, S0 = big.solve(Ad, Yd, w.S)
+    G0 = big.solve_gram(Ad, Yd, w.S)
+    torch.cuda.synchronize()
+    small = [omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=8, precision="fp32"),
+             omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=8, precision="bf16")]
+    for s in small:
+        s.solve(Ad, Yd, 8)
+    A2 = np.asfortranarray(A[:, :256])
+    small_gram = omp.OmpSolver(w.M, 256, max_batch=w.B, max_iters=8, precision="fp32")
+    small_gram.solve_gram(dev_dict(A2), Yd, 8)
+    torch.cuda.synchronize()
+    X1, S1 = big.solve(Ad, Yd, w.S)
+    G1 = big.solve_gram(Ad, Yd, w.S)
+    torch.cuda.synchronize()
+    assert np.array_equal(S0.cpu().numpy(), S1.cpu().numpy())
+    assert np.array_equal(X0.cpu().numpy().view(np.uint32), X1.cpu().numpy().view(np.uint32))
+    assert np.array_equal(G0[1].cpu().numpy(), G1[1].cpu().numpy())
+    for s in small + [small_gram, big]:
+        s.close()

@@ -257,9 +257,11 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
           vi[t] = 0x7fffffff;
         }
       // Candidates come out best first; one more than 2 rescore_eps ||r|| below the best has an
-      // FP32 score strictly below the best one's, so the rescoring stops before it.
-      const bool bound = ws.rescore_eps > 0.f && rprev > 1e-30f;
-      const float win = 2.f * ws.rescore_eps * rprev;
+      // FP32 score strictly below the best one's, so the rescoring stops before it. FP8 scores
+      // leave out the residual's scale qs, so the window is taken in their units.
+      const float qs = ws.prec == OMP_PREC_FP8_E4M3 ? ws.sr[k & 1][p] : 1.f;
+      const bool bound = ws.rescore_eps > 0.f && rprev > 1e-30f && qs > 0.f;
+      const float win = bound ? 2.f * ws.rescore_eps * rprev / qs : 0.f;
       float s_first = 0.f;
       int nres = ws.topk;
       for (int sel = 0; sel < ws.topk; ++sel) {
@@ -312,8 +314,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       // missing second.
       if (lane == 0) {
         const float lead = gs.top2[0] - fmaxf(gs.top2[1], tau_used);
-        gs.scal[2] = (ws.rescore_eps > 0.f && rprev > 1e-30f && gs.cidx[0] >= 0 &&
-                      lead > 2.f * ws.rescore_eps * rprev) ? 1 : 0;
+        gs.scal[2] = (bound && gs.cidx[0] >= 0 && lead > win) ? 1 : 0;
       }
     }
     group_sync(W, grp);

@@ -205,13 +205,15 @@ SHORTCUT_CASES = {
 }
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("case", sorted(SHORTCUT_CASES))
-def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case):
-    """BF16 skips the FP32 rescoring when the quantised best leads the second by more than twice
-    the quantisation error bound, and its correlation drops columns below the pruning threshold
-    that the previous step's update derived from its runner-up candidates. Neither may change a
-    pick: the supports, coefficients and residual norms must be bit-identical to always
-    rescoring with no pruning (OMP_RESCORE_ALWAYS=1 turns both off)."""
+def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case, prec):
+    """The quantised paths skip the FP32 rescoring when the quantised best leads the second by
+    more than twice the quantisation error bound, and rescore only the candidates within that
+    window otherwise; BF16 also drops, in its correlation, columns below the pruning threshold
+    that the previous step's update derived from its runner-up candidates. None of it may change
+    a pick: the supports, coefficients and residual norms must be bit-identical to rescoring all
+    eight candidates with no pruning (OMP_RESCORE_ALWAYS=1 turns the bound off)."""
     from paper_2407_06434_gb300 import omp
     name, over, seed = SHORTCUT_CASES[case]
     w = gen.get_config(name, **over)
@@ -225,7 +227,7 @@ def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case):
     out = {}
     for always in ("0", "1"):
         monkeypatch.setenv("OMP_RESCORE_ALWAYS", always)
-        s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
+        s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
         X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, 0.0, diagnostics=True)
         torch.cuda.synchronize()
         out[always] = (X.cpu().numpy(), sup.cpu().numpy(), resid.cpu().numpy())

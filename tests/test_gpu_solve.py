@@ -202,6 +202,10 @@ SHORTCUT_CASES = {
     # threshold bound are large
     "coherent_512x4096": ("coherent_4096x32768_s64_b16384",
                           dict(M=512, N=4096, B=1024, S=40, s_min=40, s_max=40), 5),
+    # uneven sparsity with a relative eps stop: signals retire at different steps, so the
+    # compaction moves rows, operand rows and thresholds to new positions
+    "eps_uneven_512x4096": ("gaussian_2048x16384_s4to128_b8192_lownoise",
+                            dict(M=512, N=4096, B=1500, S=48, s_min=4, s_max=44), 7),
 }
 
 
@@ -228,10 +232,13 @@ def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case, prec):
     for always in ("0", "1"):
         monkeypatch.setenv("OMP_RESCORE_ALWAYS", always)
         s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
-        X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, 0.0, diagnostics=True)
+        X, sup, n_iter, resid, stop = s.solve(Ad, Yd, w.S, w.eps, diagnostics=True)
         torch.cuda.synchronize()
         out[always] = (X.cpu().numpy(), sup.cpu().numpy(), resid.cpu().numpy())
         assert omp.omp_get_error(s.h)[1] == 0
+        if w.eps > 0:
+            n = n_iter.cpu().numpy()
+            assert np.mean(n < w.S) > 0.5 and len(np.unique(n)) > 10   # many retirement steps
         s.close()
     assert np.array_equal(out["0"][1], out["1"][1])
     assert np.array_equal(out["0"][0].view(np.uint32), out["1"][0].view(np.uint32))

@@ -43,6 +43,15 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// (s, e) <- s + x with the rounding error of the sum added into e exactly (two-sum)
+__device__ __forceinline__ void two_sum(float& s, float& e, float x) {
+  const float t = __fadd_rn(s, x);
+  const float xv = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, xv)), __fsub_rn(x, xv));
+  s = t;
+  e = __fadd_rn(e, err);
+}
+
 // 16-byte global -> shared copy (L2 only) that holds no register while in flight
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
@@ -132,23 +141,43 @@ __device__ __forceinline__ void append_column(const Ws& ws, const GroupSmem& gs,
       if (j < kk && i <= j) zl[t] = fmaf(Fr[static_cast<size_t>(j) * (j + 1) / 2 + i], wi, zl[t]);
     }
   }
-  double zz = 0.0;
+  // ||z||^2 as an unevaluated sum hi + lo of FP32 numbers: each square is split exactly by an
+  // FMA and the sums are error-free (Knuth's two-sum), so the FP64 Schur complement below gets
+  // ||z||^2 to about 2^-42 relative (far inside the FP32 error of z itself) without FP64 work
+  // per lane, which GB300 issues at a small fraction of its FP32 rate.
+  float zh = 0.f, zlo = 0.f;
 #pragma unroll
   for (int t = 0; t < NB; ++t) {
     const int j = lane + 32 * t;
     if (j < kk) {
       gs.z[j] = zl[t];
-      zz += static_cast<double>(zl[t]) * static_cast<double>(zl[t]);
+      const float p = __fmul_rn(zl[t], zl[t]);
+      zlo = __fadd_rn(zlo, fmaf(zl[t], zl[t], -p));
+      two_sum(zh, zlo, p);
     }
   }
-  zz = warp_sum(zz);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, zh, o);
+    zlo = __fadd_rn(zlo, __shfl_xor_sync(0xffffffffu, zlo, o));
+    two_sum(zh, zlo, oh);
+  }
+  const double zz = static_cast<double>(zh) + static_cast<double>(zlo);
   const double nrm2 = ws.norm2[ns];
   const double delta = nrm2 - zz;
   const bool dep = !(delta > kDepRtol * nrm2);
   if (lane == 0) gs.scal[1] = dep ? 1 : 0;
   __syncwarp();
   if (dep) return;
-  const double gamma = 1.0 / sqrt(delta);
+  // gamma = 1/sqrt(delta): the FP32 reciprocal square root as a seed, then one Newton-Raphson
+  // step y <- y (3 - delta y^2) / 2 in FP64 (the error squares: about 2^-43 relative)
+  double gamma;
+  if (delta > 1e-36 && delta < 1e36) {
+    const double y0 = static_cast<double>(rsqrtf(static_cast<float>(delta)));
+    gamma = y0 * (1.5 - 0.5 * delta * y0 * y0);
+  } else {
+    gamma = 1.0 / sqrt(delta);
+  }
   // u_i = sum_{j>=i} F[i,j] z_j, lane slot i; one coalesced column per j
   float ul[NB];
 #pragma unroll

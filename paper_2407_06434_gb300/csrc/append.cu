@@ -523,11 +523,12 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
 #pragma unroll
   for (int t = 0; t < V; ++t) bp += q[t].x * r[t].x + q[t].y * r[t].y + q[t].z * r[t].z + q[t].w * r[t].w;
   bp = warp_sum_f(bp);
-  if (lane == 0) gs.part[wig] = bp;
+  // per-warp partials of b and ||r||^2 (FP32 sums of FP32 products: no FP64 needed here)
+  float* pf = reinterpret_cast<float*>(gs.part);
+  if (lane == 0) pf[wig] = bp;
   group_sync(W, grp);
-  double b = 0.0;
-  for (int w = 0; w < W; ++w) b += gs.part[w];  // W <= 8 partials
-  const float bf = static_cast<float>(b);
+  float bf = 0.f;
+  for (int w = 0; w < W; ++w) bf += pf[w];  // W <= 8 partials
   float4* rw = reinterpret_cast<float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
   float rr = 0.f;
 #pragma unroll
@@ -605,21 +606,20 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       }
     }
   }
-  if (lane == 0) gs.part[8 + wig] = rr;
+  if (lane == 0) pf[8 + wig] = rr;
   group_sync(W, grp);
+  float rk = 0.f;  // ||r_k||, first warp's lane 0
   if (wig == 0 && lane == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
-    const double rn = sqrt(tot);
-    const double rp = static_cast<double>(rprev);
-    ws.bv[static_cast<size_t>(id) * ws.Smax + kk] = b;
+    float tot = 0.f;
+    for (int w = 0; w < W; ++w) tot += pf[8 + w];
+    rk = sqrtf(tot);
+    const float rn = rk;
+    ws.bv[static_cast<size_t>(id) * ws.Smax + kk] = static_cast<double>(bf);
     ws.sup[static_cast<size_t>(id) * ws.Smax + kk] = ns;
-    ws.drop[static_cast<size_t>(id) * ws.Smax + kk] =
-        rp > 0.0 ? static_cast<float>((b * b) / (rp * rp)) : 0.f;
+    ws.drop[static_cast<size_t>(id) * ws.Smax + kk] = rprev > 0.f ? (bf / rprev) * (bf / rprev) : 0.f;
     ws.niter[id] = kk + 1;
-    ws.rnorm[id] = static_cast<float>(rn);
-    const double thr = eps_rel ? static_cast<double>(eps) * static_cast<double>(ynorm)
-                               : static_cast<double>(eps);
+    ws.rnorm[id] = rn;
+    const float thr = eps_rel ? eps * ynorm : eps;
     int cont = 1;
     if (rn <= thr) {
       cont = 0;
@@ -640,9 +640,6 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   // candidate that changes it: the next correlation drops such columns before its top-8
   // insertion.
   if (ws.tau && wig == 0 && lane == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < W; ++w) tot += gs.part[8 + w];
-    const float rk = static_cast<float>(sqrt(tot));
     float best = 0.f;
     for (int c = 0; c < 2 && c < ws.topk; ++c) {
       const int n = gs.cidx[c];

@@ -43,15 +43,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// (s, e) <- s + x with the rounding error of the sum added into e exactly (two-sum)
-__device__ __forceinline__ void two_sum(float& s, float& e, float x) {
-  const float t = __fadd_rn(s, x);
-  const float xv = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, xv)), __fsub_rn(x, xv));
-  s = t;
-  e = __fadd_rn(e, err);
-}
-
 // 16-byte global -> shared copy (L2 only) that holds no register while in flight
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(

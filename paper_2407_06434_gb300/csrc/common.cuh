@@ -160,6 +160,16 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
   return out;
 }
 
+// (s, e) <- s + x with the rounding error of the sum added into e exactly (Knuth's two-sum):
+// s + e carries a sum of FP32 numbers to about twice FP32 precision with FP32 arithmetic only
+__device__ __forceinline__ void two_sum(float& s, float& e, float x) {
+  const float t = __fadd_rn(s, x);
+  const float xv = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, xv)), __fsub_rn(x, xv));
+  s = t;
+  e = __fadd_rn(e, err);
+}
+
 // Iteration index of a per-iteration kernel: the launch's own k, or, when the launch passes -1
 // (the body of the graph's device-side while loop, identical for every iteration), the counter
 // that the loop advances.

@@ -91,6 +91,36 @@ __device__ __forceinline__ double bsum(double v, double* red) {
   return t;
 }
 
+// Sum of the block's (hi, lo) pairs (each an unevaluated FP32 sum), as a double; every thread
+// gets the total.
+template <int W>
+__device__ __forceinline__ double bsum2(float hi, float lo, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = __fadd_rn(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    two_sum(hi, lo, oh);
+  }
+  if (W > 1) {
+    float* rf = reinterpret_cast<float*>(red);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      rf[2 * warp] = hi;
+      rf[2 * warp + 1] = lo;
+    }
+    __syncthreads();
+    hi = rf[0];
+    lo = rf[1];
+#pragma unroll
+    for (int i = 1; i < W; ++i) {
+      lo = __fadd_rn(lo, rf[2 * i + 1]);
+      two_sum(hi, lo, rf[2 * i]);
+    }
+    __syncthreads();
+  }
+  return static_cast<double>(hi) + static_cast<double>(lo);
+}
+
 // ||y - A_S x||^2 for the first n picks, x = F b (FP64 back-substitution into g.z); with `store`
 // the residual replaces y in R32. Called by the whole block.
 template <int W>
@@ -206,22 +236,33 @@ __global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S,
     const double nrm2 = ws.norm2[ns];
     const float cn = g.c[ns];
     bsync<W>();
-    // ---- z_j = sum_{i<=j} F[i,j] w_i (thread j, j + T, ...), ||z||^2 in FP64
-    double zz = 0.0;
+    // ---- z_j = sum_{i<=j} F[i,j] w_i (thread j, j + T, ...); ||z||^2 as an exact FP32
+    // double-float sum (squares split by an FMA, two-sum additions), which carries it far
+    // beyond the FP32 accuracy of z without FP64 arithmetic per thread
+    float zh = 0.f, zlo = 0.f;
     for (int j = tid; j < k; j += T) {
       const float* col = g.Fs + static_cast<size_t>(j) * (j + 1) / 2;
       float zj = 0.f;
       for (int i = 0; i <= j; ++i) zj = fmaf(col[i], g.w[i], zj);
       g.z[j] = zj;
-      zz += static_cast<double>(zj) * zj;
+      const float p = __fmul_rn(zj, zj);
+      zlo = __fadd_rn(zlo, fmaf(zj, zj, -p));
+      two_sum(zh, zlo, p);
     }
-    zz = bsum<W>(zz, g.rd);  // (its barrier also publishes z)
+    const double zz = bsum2<W>(zh, zlo, g.rd);  // (its barrier also publishes z)
     const double delta = nrm2 - zz;
     if (!(delta > kDepRtol * nrm2)) {
       stop = kStopDependent;
       break;
     }
-    const double gamma = 1.0 / sqrt(delta);
+    // gamma = 1/sqrt(delta): FP32 reciprocal square root seed, one FP64 Newton-Raphson step
+    double gamma;
+    if (delta > 1e-36 && delta < 1e36) {
+      const double y0 = static_cast<double>(rsqrtf(static_cast<float>(delta)));
+      gamma = y0 * (1.5 - 0.5 * delta * y0 * y0);
+    } else {
+      gamma = 1.0 / sqrt(delta);
+    }
     bsync<W>();
     // ---- F[:,k] = [-gamma F z ; gamma]: u_i = sum_{j>=i} F[i,j] z_j (thread i, i + T, ...)
     const size_t off = static_cast<size_t>(k) * (k + 1) / 2;

@@ -3,7 +3,8 @@
 //
 // Iteration k (0-based; the paper's k+1), following Sec. 2.3:
 //   n*    the correlation's pick (FP32 path), or the best of the merged top-8 rescored in FP32
-//         (quantised paths; skipped when a rigorous error bound shows the quantised best wins)
+//         (quantised paths; only the candidates within twice a rigorous score error bound of the
+//         quantised best are rescored, none when the best leads by more)
 //   w     = A_S^T a_{n*}          read from the Gram matrix row n* (Sec. 2.2 precompute)
 //   z     = F_k^T w               FP32, on an FP32 copy of F staged in shared memory
 //   delta = ||a_{n*}||^2 - ||z||^2 in FP64; the atom is dependent if delta <= 1e-10 ||a_{n*}||^2
@@ -11,13 +12,16 @@
 //   F[:,k] = [-gamma F_k z ; gamma]  (stored in FP64 and FP32)
 //   q     = A_{S+n*} F[:,k]       the new orthonormal direction (FP32 gather of k+1 atom rows)
 //   b_k   = q^T r,  r <- r - b_k q (y_hat = A_k F_k (A_k F_k)^T y built one term at a time)
-// and, with one warp per signal, the next step's quantised operand row at this position.
+// and, with one warp per signal, the next step's quantised operand row at this position, and
+// (BF16) the next correlation's pruning threshold from the exact FP32 correlation of the new
+// residual with the best candidate that was not picked.
 //
 // Layout of the work: the residual and q live in registers, sliced over the block's lanes in
 // float4 slots (slot s of a row belongs to lane s mod 32 of warp (s / 32) mod W). The small
 // triangular work runs in the first warp, lane-parallel over rows or columns of F. GB300 issues
-// FP64 at a small fraction of its FP32 rate, so only the Schur complement, gamma and the stored
-// factor are FP64; their FP32 inputs (w from the FP32 Gram matrix) carry no more precision.
+// FP64 at a small fraction of its FP32 rate, so only the Schur complement, gamma (an FP32
+// seed and one Newton step) and the stored factor are FP64; their FP32 inputs (w from the FP32
+// Gram matrix) carry no more precision, and ||z||^2, b and ||r|| are FP32 sums.
 #include "common.cuh"
 
 namespace ompk {
@@ -67,7 +71,7 @@ struct GroupSmem {
   int* sup;      // Smax + 1: support including n*
   float* cpart;  // 8 x 8: rescoring partial dot products [candidate][warp]
   int* cidx;     // 8
-  double* part;  // 16: per-warp partials of b and ||r||^2
+  float* part;   // 16: per-warp partials of b [0, 8) and of ||r||^2 [8, 16)
   int* scal;     // 4: n*, dependent flag, rescoring skipped, candidates to rescore
   float* top2;   // 2: the merged lists' best and second-best quantised scores
   float* rinv;   // 2: inverse norms of the two best merged candidates (threshold on)
@@ -87,7 +91,7 @@ __host__ __device__ __forceinline__ size_t row_floats(const Ws& ws) {
 __host__ __device__ __forceinline__ size_t group_bytes(const Ws& ws) {
   const int Smax = ws.Smax;
   const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
-                   8 * 4 + 16 * 8 + 16 + 8 + 8 + row_floats(ws) * 4 +
+                   8 * 4 + 16 * 4 + 16 + 8 + 8 + row_floats(ws) * 4 +
                    (tri_floats(Smax) * 4 + 15) / 16 * 16;
   return (b + 15) / 16 * 16;
 }
@@ -100,8 +104,8 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, co
   g += (tri_floats(Smax) * 4 + 15) / 16 * 16;
   s.rows = reinterpret_cast<float*>(g);  // 16-byte aligned too
   g += row_floats(ws) * 4;
-  s.part = reinterpret_cast<double*>(g);
-  s.f = reinterpret_cast<float*>(g + 16 * 8);
+  s.part = reinterpret_cast<float*>(g);
+  s.f = s.part + 16;
   s.sup = reinterpret_cast<int*>(s.f + Smax + 1);
   s.cpart = reinterpret_cast<float*>(s.sup + Smax + 1);
   s.cidx = reinterpret_cast<int*>(s.cpart + 64);
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   for (int t = 0; t < V; ++t) bp += q[t].x * r[t].x + q[t].y * r[t].y + q[t].z * r[t].z + q[t].w * r[t].w;
   bp = warp_sum_f(bp);
   // per-warp partials of b and ||r||^2 (FP32 sums of FP32 products: no FP64 needed here)
-  float* pf = reinterpret_cast<float*>(gs.part);
+  float* pf = gs.part;
   if (lane == 0) pf[wig] = bp;
   group_sync(W, grp);
   float bf = 0.f;

@@ -206,7 +206,23 @@ SHORTCUT_CASES = {
     # compaction moves rows, operand rows and thresholds to new positions
     "eps_uneven_512x4096": ("gaussian_2048x16384_s4to128_b8192_lownoise",
                             dict(M=512, N=4096, B=1500, S=48, s_min=4, s_max=44), 7),
+    # exact duplicates (equal scores: the lower index must win everywhere) and near-duplicates
+    # (scores within the error bounds) of the first 128 atoms, in other atom tiles
+    "duplicates_256x2048": ("gaussian_64x256_s8_b16",
+                            dict(M=256, N=2048, B=600, S=32, s_min=8, s_max=24, sigma=1e-3,
+                                 col_scale=1.0), 13),
 }
+
+
+def _duplicate_columns(A, seed):
+    """Columns 1000..1127 copy columns 0..127; columns 1500..1627 are those copies with a
+    1e-4 perturbation, renormalised."""
+    A = np.array(A, dtype=np.float64)
+    A[:, 1000:1128] = A[:, 0:128]
+    rng = np.random.default_rng(seed)
+    B = A[:, 0:128] + 1e-4 * rng.standard_normal((A.shape[0], 128))
+    A[:, 1500:1628] = B / np.linalg.norm(B, axis=0)
+    return np.asfortranarray(A.astype(np.float32))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
@@ -225,6 +241,8 @@ def test_rescoring_shortcut_and_pruning_are_exact(monkeypatch, case, prec):
     if w.dict_kind == "coherent":
         scale = np.random.default_rng(seed).uniform(0.5, 2.0, w.N).astype(np.float32)
         A = np.asfortranarray(A * scale[None, :])
+    if case.startswith("duplicates"):
+        A = _duplicate_columns(A, seed)
     Y, *_ = gen.signals(w, A, seed=seed)
     Ad = dev_dict(A)
     Yd = torch.from_numpy(Y).cuda()

@@ -331,6 +331,16 @@ omp_status omp_get_error(omp_handle h, int32_t* flags, void* stream);
 /* Human-readable name of a status code (static storage). */
 const char* omp_status_string(omp_status s);
 
+/* Host-only (no device work, callable without a GPU): the bound eps, per unit of ||a|| ||r||, on
+ * |quantised score - FP32 score| that the quantised paths use to skip or trim the FP32 rescoring
+ * and (BF16) to prune the correlation; Mp is the padded signal length. It covers rounding both
+ * operands (BF16: unit roundoff 2^-8; E4M3 with a per-row scale amax/448: 2^-4 relative in the
+ * normal range plus half the subnormal spacing of the scale), the tensor-core and FP32
+ * accumulations over Mp terms, and 1% for the rounding of norms and scales. Returns 0 for
+ * OMP_PREC_FP32, an unknown precision or Mp < 1 (no bound: the rescoring always runs).
+ * The readings behind it: the rescoring of Sec. 3.7's reduced precision, our design. */
+float omp_score_error_bound(int32_t precision, int64_t Mp);
+
 #ifdef __cplusplus
 }
 #endif

@@ -292,6 +292,31 @@ const char* omp_status_string(omp_status s) {
   return "OMP_ERR_UNKNOWN";
 }
 
+// |quantised score - FP32 score| <= bound ||a|| ||r|| (the FP8 score taken in the units of the
+// residual's scale). BF16 rounding of a and r (unit roundoff u = 2^-8) gives 2u + u^2 of
+// sum |a_m r_m| <= ||a|| ||r||. E4M3 with a per-row scale s = amax / 448 rounds each element to
+// within u |x| + beta s, u = 2^-4 in the normal range and beta = 2^-10 (half the subnormal
+// spacing) below it; with s <= ||x|| / 448 and sum |x_m| <= sqrt(Mp) ||x|| that is
+// 2u + u^2 + 2 sqrt(Mp) b (1 + u) + Mp b^2 with b = 2^-10 / 448. The tensor-core accumulation is
+// allowed 2^-22 and the FP32 rescoring 2^-24 per addition over Mp terms; 1% covers the rounding
+// of inv_norm, of the scales and of the stored ||r||.
+float omp_score_error_bound(int32_t precision, int64_t Mp) {
+  if (Mp < 1) return 0.f;
+  const double m = static_cast<double>(Mp);
+  const double g_tc = m * std::ldexp(1.0, -22) / (1.0 - m * std::ldexp(1.0, -22));
+  const double g_32 = m * std::ldexp(1.0, -24) / (1.0 - m * std::ldexp(1.0, -24));
+  if (precision == OMP_PREC_BF16) {
+    const double u = std::ldexp(1.0, -8);
+    return static_cast<float>(1.01 * (2 * u + u * u + (1 + u) * (1 + u) * g_tc + g_32));
+  }
+  if (precision == OMP_PREC_FP8_E4M3) {
+    const double u = std::ldexp(1.0, -4), b = std::ldexp(1.0, -10) / 448.0, sb = std::sqrt(m) * b;
+    return static_cast<float>(
+        1.01 * (2 * u + u * u + 2 * sb * (1 + u) + m * b * b + (1 + u + sb) * (1 + u + sb) * g_tc + g_32));
+  }
+  return 0.f;
+}
+
 omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   if (!desc || !out) return OMP_ERR_INVALID_ARGUMENT;
   *out = nullptr;
@@ -328,31 +353,9 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ws.Bpad = (ws.Bmax + kSigTile - 1) / kSigTile * kSigTile;
   ws.prec = d.precision;
   ws.topk = d.precision == OMP_PREC_FP32 ? 1 : h->d.rescore_topk;
-  // |quantised score - FP32 score| <= rescore_eps ||r|| (||a|| inv_norm = 1, the FP8 score taken
-  // in the units of the residual's scale). BF16 rounding of a and r (unit roundoff u = 2^-8)
-  // gives 2u + u^2 of sum |a_m r_m| <= ||a|| ||r||. E4M3 with a per-row scale s = amax / 448
-  // rounds each element to within u |x| + beta s, u = 2^-4 in the normal range and beta = 2^-10
-  // (half the subnormal spacing) below it; with s <= ||x|| / 448 and sum |x_m| <= sqrt(Mp) ||x||
-  // that is 2u + u^2 + 2 sqrt(Mp) b (1 + u) + Mp b^2 with b = 2^-10 / 448. The tensor-core
-  // accumulation is allowed 2^-22 and the FP32 rescoring 2^-24 per addition over Mp terms; 1%
-  // covers the rounding of inv_norm, of the scales and of the stored ||r||.
-  // (test hook: OMP_RESCORE_ALWAYS=1 turns the bound, and all that uses it, off)
+  // (test hook: OMP_RESCORE_ALWAYS=1 turns the score bound, and all that uses it, off)
   const char* always = std::getenv("OMP_RESCORE_ALWAYS");
-  const double m = static_cast<double>(ws.Mp);
-  const double g_tc = m * std::ldexp(1.0, -22) / (1.0 - m * std::ldexp(1.0, -22));
-  const double g_32 = m * std::ldexp(1.0, -24) / (1.0 - m * std::ldexp(1.0, -24));
-  if (always && std::atoi(always) == 1) {
-    ws.rescore_eps = 0.f;
-  } else if (ws.prec == OMP_PREC_BF16) {
-    const double u = std::ldexp(1.0, -8);
-    ws.rescore_eps = static_cast<float>(1.01 * (2 * u + u * u + (1 + u) * (1 + u) * g_tc + g_32));
-  } else if (ws.prec == OMP_PREC_FP8_E4M3) {
-    const double u = std::ldexp(1.0, -4), b = std::ldexp(1.0, -10) / 448.0, sb = std::sqrt(m) * b;
-    ws.rescore_eps = static_cast<float>(
-        1.01 * (2 * u + u * u + 2 * sb * (1 + u) + m * b * b + (1 + u + sb) * (1 + u + sb) * g_tc + g_32));
-  } else {
-    ws.rescore_eps = 0.f;
-  }
+  ws.rescore_eps = always && std::atoi(always) == 1 ? 0.f : omp_score_error_bound(ws.prec, ws.Mp);
   // padded to 4 entries so each signal's FP32 factor starts on a 16-byte boundary
   ws.Fstride = (static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2 + 3) / 4 * 4;
   ws.upd_w = update_default_warps(ws.Mp);

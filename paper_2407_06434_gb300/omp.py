@@ -37,7 +37,8 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_get_thresholds", "omp_proposal_calibrate", "omp_topk_rows",
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
            "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
-           "omp_loop_passes", "omp_read_bandwidth_probe", "omp_solve_batch_gram"]
+           "omp_loop_passes", "omp_read_bandwidth_probe", "omp_solve_batch_gram",
+           "omp_score_error_bound"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -95,6 +96,7 @@ def load(path: Optional[str] = None):
         "omp_loop_passes": (_I32, [_P, ctypes.POINTER(_I32), _P]),
         "omp_solve_batch_gram": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
         "omp_read_bandwidth_probe": (_I32, [_P, _I64, _I32, _P, _I32, _P]),
+        "omp_score_error_bound": (_F32, [_I32, _I64]),
         "omp_proposal_desc_default": (None, [ctypes.POINTER(omp_proposal_desc)]),
         "omp_proposal_create": (_I32, [_P, ctypes.POINTER(omp_proposal_desc), ctypes.POINTER(_P)]),
         "omp_proposal_destroy": (_I32, [_P]),
@@ -280,6 +282,11 @@ def omp_correlate_argmax_noalloc(A, R, idx_out, score_out, stream=None):
 
 def omp_status_string(status: int) -> str:
     return load().omp_status_string(status).decode()
+
+
+def omp_score_error_bound(precision: int, Mp: int) -> float:
+    """Bound per unit of ||a|| ||r|| on |quantised score - FP32 score| (host only, no GPU)."""
+    return float(load().omp_score_error_bound(precision, Mp))
 
 
 def omp_solve_batch_trace(h: Handle, A, Y, S: int, eps: float, X_out, support_out, drop_out,

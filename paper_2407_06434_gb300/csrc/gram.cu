@@ -34,7 +34,8 @@ namespace {
 
 
 struct GSmem {
-  double* rd;  // 9: block reduction scratch
+  double* rd;  // 12: block reduction scratch [0, 8); the step's gamma [8], b_k [9], and whether
+               // the running ||r||^2 is near the threshold [10], formed by thread 0
   float* rs;   // 8: per-warp best scores
   int* ri;     // 9: per-warp best atoms, then the block's
   float* c;    // Np4: current correlations (N rounded up to 4, tail zero)
@@ -48,7 +49,7 @@ struct GSmem {
 __host__ __device__ __forceinline__ int np4(int N) { return (N + 3) / 4 * 4; }
 
 __host__ __device__ __forceinline__ size_t gs_bytes(int N, int S) {
-  size_t b = 9 * 8 + 8 * 4 + 9 * 4 + 4 + static_cast<size_t>(np4(N)) * 4 +
+  size_t b = 12 * 8 + 8 * 4 + 9 * 4 + 12 + static_cast<size_t>(np4(N)) * 4 +
              static_cast<size_t>(S) * (S + 1) / 2 * 4 + static_cast<size_t>(S) * 4 * 2 +
              static_cast<size_t>(S + 1) * 4 + static_cast<size_t>(S) * 4;
   return (b + 15) / 16 * 16;
@@ -57,9 +58,9 @@ __host__ __device__ __forceinline__ size_t gs_bytes(int N, int S) {
 __device__ __forceinline__ GSmem gs_layout(unsigned char* base, int N, int S) {
   GSmem g;
   g.rd = reinterpret_cast<double*>(base);
-  g.rs = reinterpret_cast<float*>(base + 9 * 8);
+  g.rs = reinterpret_cast<float*>(base + 12 * 8);
   g.ri = reinterpret_cast<int*>(g.rs + 8);
-  g.c = reinterpret_cast<float*>(base + 9 * 8 + 8 * 4 + 9 * 4 + 4);  // 16-byte aligned
+  g.c = reinterpret_cast<float*>(base + 12 * 8 + 8 * 4 + 9 * 4 + 12);  // 16-byte aligned
   g.Fs = g.c + np4(N);
   g.w = g.Fs + static_cast<size_t>(S) * (S + 1) / 2;
   g.z = g.w + S;
@@ -250,20 +251,36 @@ __global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S,
       two_sum(zh, zlo, p);
     }
     const double zz = bsum2<W>(zh, zlo, g.rd);  // (its barrier also publishes z)
-    const double delta = nrm2 - zz;
-    if (!(delta > kDepRtol * nrm2)) {
+    // The step's scalars, formed once by thread 0 (GB300 issues FP64 at a small fraction of
+    // its FP32 rate, so the block does not repeat it): gamma = 1/sqrt(delta) from an FP32
+    // reciprocal square root seed and one FP64 Newton-Raphson step (0 for a dependent atom),
+    // b_k = gamma c_n*, the running ||r||^2 and whether it has come near the threshold.
+    if (tid == 0) {
+      const double delta = nrm2 - zz;
+      double gamma = 0.0, bk = 0.0;
+      if (delta > kDepRtol * nrm2) {
+        if (delta > 1e-36 && delta < 1e36) {
+          const double y0 = static_cast<double>(rsqrtf(static_cast<float>(delta)));
+          gamma = y0 * (1.5 - 0.5 * delta * y0 * y0);
+        } else {
+          gamma = 1.0 / sqrt(delta);
+        }
+        bk = gamma * static_cast<double>(cn);
+        const double r2prev = r2;
+        r2 -= bk * bk;
+        bvg[k] = bk;
+        ws.drop[static_cast<size_t>(b) * ws.Smax + k] = r2prev > 0.0 ? static_cast<float>((bk * bk) / r2prev) : 0.f;
+      }
+      g.rd[8] = gamma;
+      g.rd[9] = bk;
+      g.rd[10] = thr > 0.0 && r2 <= 4.0 * thr * thr + 2e-5 * static_cast<double>(yn) * yn ? 1.0 : 0.0;
+    }
+    bsync<W>();
+    const double gamma = g.rd[8];
+    if (!(gamma > 0.0)) {
       stop = kStopDependent;
       break;
     }
-    // gamma = 1/sqrt(delta): FP32 reciprocal square root seed, one FP64 Newton-Raphson step
-    double gamma;
-    if (delta > 1e-36 && delta < 1e36) {
-      const double y0 = static_cast<double>(rsqrtf(static_cast<float>(delta)));
-      gamma = y0 * (1.5 - 0.5 * delta * y0 * y0);
-    } else {
-      gamma = 1.0 / sqrt(delta);
-    }
-    bsync<W>();
     // ---- F[:,k] = [-gamma F z ; gamma]: u_i = sum_{j>=i} F[i,j] z_j (thread i, i + T, ...)
     const size_t off = static_cast<size_t>(k) * (k + 1) / 2;
     for (int i = tid; i < k; i += T) {
@@ -286,10 +303,9 @@ __global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S,
       supg[k] = ns;
     }
     bsync<W>();
-    const double bk = gamma * static_cast<double>(cn);
     // ---- c <- c - b_k sum_j f_j G[s_j, :], in panels: thread t takes 4 atoms per 4T, 16-byte
     // Gram loads (scalar ones when N is not a multiple of 4)
-    const float bf = static_cast<float>(bk);
+    const float bf = static_cast<float>(g.rd[9]);
     for (int p0 = 0; p0 < N; p0 += 4 * T * VP) {
       float4 acc[VP];
 #pragma unroll
@@ -332,16 +348,10 @@ __global__ void __launch_bounds__(32 * W) gram_solve_kernel(Ws ws, int B, int S,
         }
       }
     }
-    const double r2prev = r2;
-    r2 -= bk * bk;
-    if (tid == 0) {
-      bvg[k] = bk;
-      ws.drop[static_cast<size_t>(b) * ws.Smax + k] = r2prev > 0.0 ? static_cast<float>((bk * bk) / r2prev) : 0.f;
-    }
     bsync<W>();  // c updated before the next selection
     // The running ||r||^2 carries the FP32 error of the b_k (about k 2^-24 ||y||^2), so near
     // the threshold the stop test uses the residual itself, formed from the support.
-    if (thr > 0.0 && r2 <= 4.0 * thr * thr + 2e-5 * static_cast<double>(yn) * yn) {
+    if (g.rd[10] != 0.0) {
       const double rr = residual_norm2<W>(ws, g, Fg, bvg, b, k + 1, false);
       if (rr <= thr * thr) {
         stop = kStopEps;

@@ -64,7 +64,10 @@ typedef struct omp_desc {
   int64_t max_batch;     /* largest B any solve on this handle will pass, >= 1 */
   int32_t max_iters;     /* largest S any solve will pass, 1 <= max_iters <= min(M, N, 256) */
   int32_t precision;     /* omp_precision */
-  int32_t rescore_topk;  /* quantised paths: candidates rescored in FP32, 1..8 (0 means 8) */
+  int32_t rescore_topk;  /* quantised paths: candidates kept for the FP32 rescoring, 1..8 (0 means
+                            8); of these only the ones within twice the score error bound
+                            (omp_score_error_bound) of the quantised best are rescored, and none
+                            when the best leads by more, which picks the same atom */
   int32_t eps_relative;  /* 1: stop when ||r_k|| <= eps * ||y||; 0: when ||r_k|| <= eps (Alg. 1) */
   int32_t use_graph;     /* capture each (B, S, eps) solve once as a CUDA graph and replay it:
                             1 with the S iterations unrolled (kernels of an iteration with no live

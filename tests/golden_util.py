@@ -26,3 +26,18 @@ def load(name):
 
 
 FIXTURES = ["worked_example_3x4.json", "dependent_atom_3x3.json", "tie_duplicate_2x3.json"]
+
+
+def load_candidates(name):
+    """A candidate-restricted fixture: the common fields as load(), and each case's numbers."""
+    d = load(name)
+    d["cand"] = np.array(d["cand"], dtype=np.int64)
+    for c in d["cases"]:
+        c["tau"] = np.array([_num(v) for v in c["tau"]])
+        for key in ("coef", "resid_trace", "margin", "drops"):
+            if key in c:
+                c[key] = np.array([_num(v) for v in c[key]])
+    return d
+
+
+CANDIDATE_FIXTURES = ["candidates_fallback_3x4.json", "candidates_unequal_norms_3x3.json"]

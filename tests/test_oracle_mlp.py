@@ -104,3 +104,75 @@ def test_candidate_reference_reduces_to_plain_omp():
         others = np.setdiff1d(np.arange(256), [ref.support[0, 0]])
         r, fb = omp.omp_candidates_reference(A, Y[b], 8, others[:40], np.full(8, 0.99))
         assert fb == 0 and np.array_equal(r.support, ref.support)
+
+
+def _orthonormal_dictionary(seed, M=16):
+    """Q D: an orthonormal basis with columns rescaled by d_n in [0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((M, M)))
+    d = rng.uniform(0.5, 2.0, M)
+    return Q, Q * d[None, :]
+
+
+def test_features_closed_form_on_an_orthonormal_dictionary():
+    """For A = Q D (Q orthonormal, D a positive diagonal) the features x = A^T y / (||a|| ||y||)
+    are Q^T y / ||y||: a unit vector whatever the column scales and the signal's scale, from
+    which Q x gives back y / ||y||. A zero signal gives zero features."""
+    Q, A = _orthonormal_dictionary(5)
+    rng = np.random.default_rng(6)
+    Y = rng.standard_normal((6, 16)) * np.array([1e-3, 1.0, 1e3, 2.0, 0.5, 7.0])[:, None]
+    Y[4] = 0.0
+    X = mlp.features(A.astype(np.float32), Y.astype(np.float32), round_bf16=False)
+    Y32 = Y.astype(np.float32).astype(np.float64)
+    for b in range(6):
+        yn = np.linalg.norm(Y32[b])
+        if yn == 0:
+            assert np.all(X[b] == 0)
+            continue
+        assert abs(np.linalg.norm(X[b]) - 1.0) < 1e-6
+        np.testing.assert_allclose(Q @ X[b], Y32[b] / yn, atol=1e-6)
+
+
+def test_features_bf16_within_the_rounding_bound():
+    """With BF16 rounding on, every feature is a BF16 number, within the bound that rounding y
+    and a (unit roundoff u = 2^-8, relative error at most 2u + u^2 per product, and
+    sum |a_m y_m| <= ||a|| ||y||) and rounding the result (u |x|) give: 2u + u^2 + u |x|."""
+    from oracle import quant
+    _, A = _orthonormal_dictionary(7, M=64)
+    rng = np.random.default_rng(8)
+    Y = rng.standard_normal((8, 64))
+    Xb = mlp.features(A.astype(np.float32), Y.astype(np.float32), round_bf16=True)
+    Xe = mlp.features(A.astype(np.float32), Y.astype(np.float32), round_bf16=False)
+    assert np.array_equal(quant.bf16_round(Xb.astype(np.float32)).astype(np.float64), Xb)
+    u = 2.0 ** -8
+    assert np.all(np.abs(Xb - Xe) <= (2 * u + u * u) * 1.001 + u * np.abs(Xe))
+    assert np.any(Xb != Xe)
+
+
+def test_logits_closed_form_without_hidden_layer():
+    """With W1 = 0 and b1 = 0 the hidden layer is GELU(0) = 0, so the logits are exactly
+    b2 + beta |x| (the skip term), with and without BF16 rounding."""
+    X, Yl, W1, b1, W2, b2 = _instance(9)
+    for rb in (False, True):
+        O = mlp.logits(X, np.zeros_like(W1), np.zeros_like(b1), W2, b2, round_bf16=rb, beta=2.5)
+        np.testing.assert_allclose(O, b2[None, :] + 2.5 * np.abs(X), rtol=0, atol=1e-15)
+
+
+def test_logits_match_the_training_forward_pass():
+    """logits() and the forward pass inside loss_and_grads() are separate code: the weighted BCE
+    evaluated here from logits() (as (1 - y + pw y) log(1 + e^o) - pw y o, an algebraically
+    equal form) equals loss_and_grads()'s loss, and a central difference of that loss in beta
+    equals loss_and_grads()'s d loss / d beta."""
+    X, Yl, W1, b1, W2, b2 = _instance(10)
+    pw = 6.0
+
+    def loss_from_logits(beta):
+        O = mlp.logits(X, W1, b1, W2, b2, round_bf16=False, beta=beta)
+        return np.mean((1 - Yl + pw * Yl) * np.logaddexp(0.0, O) - pw * Yl * O)
+
+    for beta in (0.0, 1.7, -0.8):
+        loss, *_, dbeta = mlp.loss_and_grads(X, Yl, W1, b1, W2, b2, pw, False, beta)
+        assert abs(loss_from_logits(beta) - loss) <= 1e-12 * abs(loss)
+        h = 1e-5
+        fd = (loss_from_logits(beta + h) - loss_from_logits(beta - h)) / (2 * h)
+        assert abs(fd - dbeta) <= 1e-7 * max(abs(dbeta), 1e-3)

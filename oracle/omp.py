@@ -404,3 +404,27 @@ def omp_candidates_reference(A, y, S, cand, tau, eps=0.0, eps_relative=True):
     res.support[0, :kk] = supp
     res.coef[0, :kk] = x[:kk] if kk else x
     return res, fb
+
+
+def prefix_scores(A, y, picks):
+    """Alg. 1's selection step evaluated along a given support.
+
+    For t = 0..k (k = len(picks)), r_t = y - P_t y with P_t the orthogonal projector onto the span
+    of the first t picked atoms (r_t is the least-squares residual of that prefix, as in Alg. 1).
+    Returns (scores, rnorm): scores[t, n] = |<r_t, a_n>| / ||a_n|| for t < k (FP64, zero-norm
+    atoms scoring 0) and rnorm[t] = ||r_t|| for t = 0..k. The projectors come from one Householder
+    QR of A_S (LAPACK), whose first t columns of Q span the first t picked atoms."""
+    A = np.asarray(A, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    picks = [int(p) for p in picks]
+    k = len(picks)
+    R = np.zeros((k + 1, y.shape[0]))
+    R[0] = y
+    if k:
+        Q, _ = np.linalg.qr(A[:, picks])
+        coef = Q.T @ y
+        for t in range(k):
+            R[t + 1] = R[t] - coef[t] * Q[:, t]
+    inv = _inv_or_zero(atom_norms(A))
+    scores = np.abs(R[:k] @ A) * inv[None, :]
+    return scores, np.sqrt(np.einsum("tm,tm->t", R, R))

@@ -1,5 +1,8 @@
 """Full-size workloads on the GPU (graph replay, the benchmark's launch configuration), checked
-against the FP64 oracle on sampled signals with the parity rules of tests/parity.py.
+against the FP64 oracle on 1024 seeded signals of each batch (every signal when the batch is
+smaller) with the parity rules of oracle/compare.py: identical supports wherever the oracle's
+top-two margin exceeds 1e-3, every pick after a near-tie valid along the result's own support,
+coefficients and residual norms within 1e-4.
 
 - uneven batching: 2048 x 16384, B = 8192, sparsity 4..128, eps = 1e-3 relative, S = 128, at
   noise sigma = 1e-3 (the eps stop never fires) and sigma = 1e-6 (it fires near k = s);
@@ -31,7 +34,17 @@ def lib():
     return omp
 
 
-def run_config(name, prec, n_check, **overrides):
+N_CHECK = 1024
+
+
+def check_rows(B, n=N_CHECK, seed=0):
+    """The seeded sample of signals checked against the oracle (all of them when B <= n)."""
+    if B <= n:
+        return np.arange(B)
+    return np.sort(np.random.default_rng(seed).choice(B, n, replace=False))
+
+
+def run_config(name, prec, n_check=N_CHECK, **overrides):
     from paper_2407_06434_gb300 import omp
     w = gen.get_config(name, **overrides)
     A = gen.dictionary(w)
@@ -42,7 +55,7 @@ def run_config(name, prec, n_check, **overrides):
     torch.cuda.synchronize()
     X, S_, n_iter, resid = X.cpu().numpy(), S_.cpu().numpy(), n_iter.cpu().numpy(), resid.cpu().numpy()
     s.close()
-    rows = np.linspace(0, w.B - 1, n_check).astype(int)
+    rows = check_rows(w.B, n_check)
     ref = oracle.omp_batch(A, Y[rows], w.S, w.eps, True)
     st = parity.compare(A, Y[rows], ref, S_[rows], X[rows], n_iter[rows], resid[rows], eps=w.eps,
                         rows=rows)
@@ -50,31 +63,31 @@ def run_config(name, prec, n_check, **overrides):
 
 
 def test_uneven_batch_2048x16384_bf16():
-    w, st, n_iter, S_, sup = run_config("gaussian_2048x16384_s4to128_b8192", "bf16", 24)
-    assert st["tie_diverged"] <= 2, st
+    w, st, n_iter, S_, sup = run_config("gaussian_2048x16384_s4to128_b8192", "bf16")
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st
     assert np.all(n_iter == w.S)                      # the noise floor stays above eps ||y||
 
 
 def test_uneven_batch_2048x16384_lownoise_bf16():
-    w, st, n_iter, S_, sup = run_config("gaussian_2048x16384_s4to128_b8192_lownoise", "bf16", 24)
-    assert st["tie_diverged"] <= 2, st
+    w, st, n_iter, S_, sup = run_config("gaussian_2048x16384_s4to128_b8192_lownoise", "bf16")
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st
     sp = np.sum(sup >= 0, axis=1)
     assert np.mean(np.abs(n_iter - sp) <= 2) > 0.9     # the eps stop fires near k = s
 
 
 def test_coherent_4096x32768_fp8():
-    w, st, n_iter, S_, sup = run_config("coherent_4096x32768_s64_b16384", "fp8", 16)
-    assert st["tie_diverged"] <= 2, st
+    w, st, n_iter, S_, sup = run_config("coherent_4096x32768_s64_b16384", "fp8")
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st
     assert np.all(n_iter == w.S)
 
 
 def test_learned_workload_dense_1024x8192_s48():
-    w, st, n_iter, S_, sup = run_config("gaussian_1024x8192_s48_b16384", "bf16", 24)
-    assert st["tie_diverged"] <= 2, st
+    w, st, n_iter, S_, sup = run_config("gaussian_1024x8192_s48_b16384", "bf16")
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st
 
 
 @pytest.mark.parametrize("name", ["patches_256x1024_s32_b5000", "face_8064x1207_s30_b1200",
                                   "audio_512x2048_s64_b5000"])
 def test_paper_application_shapes(name):
-    w, st, n_iter, S_, sup = run_config(name, "bf16", 24)
-    assert st["tie_diverged"] <= 3, st
+    w, st, n_iter, S_, sup = run_config(name, "bf16")
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st

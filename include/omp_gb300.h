@@ -158,8 +158,9 @@ omp_status omp_profile_read(omp_handle h, int32_t S, float* corr_ms_host, float*
  * creating a handle (omp_create allocates a whole solver's workspaces).
  *   A          device, M x N column-major dictionary (any column norms; they are computed here)
  *   R          device, B x M row-major residuals (or signals)
- *   idx_out    device, B int32: argmax_n |<r_b, a_n>| / ||a_n||, lowest index on exact ties
- *              (-1 if every atom has zero norm)
+ *   idx_out    device, B int32: argmax_n |<r_b, a_n>| / ||a_n||, lowest index on exact ties;
+ *              a zero-norm atom scores 0 (as on the handle path), so every signal gets a valid
+ *              atom index (an all-zero dictionary gives atom 0 with score 0)
  *   score_out  device, B float: that score
  * The correlation runs in FP32 on the CUDA cores. Runs on the calling thread's current device;
  * every pointer must be on it and 4-byte aligned. B > OMP_NOALLOC_MAX_SIGNALS (or any other bad

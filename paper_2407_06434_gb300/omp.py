@@ -269,12 +269,24 @@ def omp_profile_read(h: Handle, S: int, stream=None):
 
 def omp_correlate_argmax_noalloc(A, R, idx_out, score_out, stream=None):
     """Allocation-free argmax of |<r_b, a_n>| / ||a_n|| for callers that cannot allocate device
-    memory (see include/omp_gb300.h). A: (M, N) column-major; R: (B, M); idx_out: (B,) int32;
-    score_out: (B,) float32. Raises OmpError(OMP_ERR_INVALID_ARGUMENT) for
+    memory (see include/omp_gb300.h). A: (M, N) float32 column-major; R: (B, M) float32
+    contiguous; idx_out: >= B int32; score_out: >= B float32, all on one CUDA device (checked
+    here: ValueError before any call into C). Raises OmpError(OMP_ERR_INVALID_ARGUMENT) for
     B > NOALLOC_MAX_SIGNALS."""
+    if A.dim() != 2 or R.dim() != 2:
+        raise ValueError("A must be (M, N) and R (B, M)")
     M, N = A.shape
-    if A.stride() != (1, M):
-        raise ValueError("A must be column-major (stride (1, M))")
+    _check_A(A, M, N)
+    B = R.shape[0]
+    if R.dtype.is_floating_point is False or str(R.dtype) != "torch.float32":
+        raise ValueError("R must be float32")
+    if R.shape[1] != M or not R.is_contiguous():
+        raise ValueError(f"R must be a contiguous (B, {M}) tensor")
+    for name, t, dt in (("idx_out", idx_out, "torch.int32"), ("score_out", score_out, "torch.float32")):
+        if str(t.dtype) != dt or not t.is_contiguous() or t.numel() < B:
+            raise ValueError(f"{name} must be a contiguous {dt[6:]} tensor with at least {B} elements")
+    if len({str(t.device) for t in (A, R, idx_out, score_out)}) != 1 or not R.is_cuda:
+        raise ValueError("A, R, idx_out and score_out must be on the same CUDA device")
     _check(load().omp_correlate_argmax_noalloc(_ptr(A), _ptr(R), M, N, R.shape[0], _ptr(idx_out),
                                                _ptr(score_out), _stream(stream)),
            "omp_correlate_argmax_noalloc")

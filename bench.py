@@ -93,6 +93,9 @@ def oracle_cores():
     return os.cpu_count() or 1
 
 
+_ORACLE_CACHE = {}
+
+
 def time_oracle(w, A, Y, seconds_target=15.0, max_signals=None):
     """FP64 timed-mode oracle on a bounded sample: grows the sample until ~seconds_target."""
     from oracle import omp as oracle_omp
@@ -101,14 +104,34 @@ def time_oracle(w, A, Y, seconds_target=15.0, max_signals=None):
     while True:
         rows = slice(0, min(n, Y.shape[0]))
         t0 = time.perf_counter()
-        oracle_omp.omp_batch(A, Y[rows], w.S, w.eps, True)
+        ref = oracle_omp.omp_batch(A, Y[rows], w.S, w.eps, True)
         dt = time.perf_counter() - t0
         total_t, total_n = dt, rows.stop
+        _ORACLE_CACHE[(w.name, rows.stop)] = ref
         if total_t >= seconds_target / 4 or rows.stop >= Y.shape[0] or \
                 (max_signals and rows.stop >= max_signals):
             break
         n *= 2
     return total_n / total_t, total_n, total_t
+
+
+def accuracy_report(w, A, Y, n, res):
+    """Errors of a solve's results against the FP64 oracle on the first n signals of the batch:
+    per-signal coefficient error ||x - x_ref|| / ||x_ref|| (max and median), residual-norm error
+    (max relative, and max over its tolerance 1e-4 ||r|| + 1e-6 ||y||), supports that differ at a
+    top-two margin above 1e-3 (must be 0), near-tie divergences, with the parity rules of the
+    tests (a diverged signal is measured against the least squares on its own support)."""
+    from oracle import compare
+    from oracle import omp as oracle_omp
+    key = (w.name, n)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle_omp.omp_batch(A, Y[:n], w.S, w.eps, True)
+    ref = _ORACLE_CACHE[key]
+    st = compare.compare(A, Y[:n], ref, res["sup"][:n], res["X"][:n], res["n_iter"][:n],
+                         res["resid"][:n], eps=w.eps, strict=False)
+    rep = compare.error_report(st)
+    rep["reference"] = f"FP64 oracle, first {n} signals of the batch"
+    return rep
 
 
 class Clocks:
@@ -188,8 +211,9 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    def bench_form(prec):
-        solver = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
+    def bench_form(prec, gather24=False):
+        solver = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec,
+                               gather24=gather24)
         h = solver.h
         X = torch.empty((w.B, w.S), dtype=torch.float32, device=dev)
         sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
@@ -239,14 +263,18 @@ def run_gpu(args):
             t0 = time.perf_counter()
             omp.omp_solve_batch_host(h, Ad, Yh, w.S, w.eps, Xh, Sh)
             e2e_t.append(time.perf_counter() - t0)
+        # one more solve, untimed, with the per-signal diagnostics the error report uses
+        Xd, Sd, nd, rd, _ = solver.solve(Ad, Yd, w.S, w.eps, diagnostics=True)
+        torch.cuda.synchronize()
         res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live, update_warps=tuned,
                    e2e_s=float(np.sum(e2e_t)), e2e_steps=len(e2e_t),
-                   sup=sup.cpu().numpy(), X=X.cpu().numpy())
+                   sup=Sd.cpu().numpy(), X=Xd.cpu().numpy(), n_iter=nd.cpu().numpy(),
+                   resid=rd.cpu().numpy())
         solver.close()
         return res
 
     with Clocks(local) as clk:
-        chosen = bench_form(args.precision)
+        chosen = bench_form(args.precision, args.gather24)
     plain = bench_form("fp32") if args.precision != "fp32" and not args.skip_plain else None
     clocks = clk.summary()
     # L2-to-SM streaming read bandwidth (the library's probe kernel, 64 MiB buffer), measured
@@ -267,18 +295,22 @@ def run_gpu(args):
     k = np.arange(w.S)
     qbytes = 4 if args.precision == "fp32" else 0
     topk = 1 if args.precision == "fp32" else 8
-    # update: gather of k+1 FP32 atom rows + topk FP32 rescoring rows (quantised paths)
-    # + residual read and write, per live signal
-    upd_bytes = live * 4.0 * w.M * ((k + 1) + (topk if topk > 1 else 0) + 2)
+    # update: gather of k+1 atom rows (4 bytes an element, 3 with the 24-bit copy) + topk FP32
+    # rescoring rows (quantised paths) + residual read and write, per live signal
+    gb = 3.0 if args.gather24 else 4.0
+    upd_bytes = live * w.M * (gb * (k + 1) + 4.0 * ((topk if topk > 1 else 0) + 2))
     if corr_ms.sum() >= upd_ms.sum():
         dur = corr_ms.mean() / 1e3
         achieved = float(flops_corr.mean() / dur / 1e12)
         if args.precision == "fp32":
             peak, unit, bound, src = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu", "nominal"
         else:
-            key = "bf16_tflops_sustained"
+            # each correlation launch is timed on its own (tens of microseconds inside a solve of
+            # a few milliseconds), so the burst peak applies; FP8 takes 2x (the nominal ratio)
+            key = "bf16_tflops"
             peak = peaks.get(key, PEAKS_FALLBACK[key]) * (2.0 if args.precision == "fp8" else 1.0)
-            unit, bound, src = "TFLOP/s", "tensor", peak_src
+            unit, bound, src = "TFLOP/s", "tensor", peak_src + (" burst" + (" x2 (fp8)" if
+                                                                           args.precision == "fp8" else ""))
         kern = "correlate"
         alg = float(flops_corr.mean())
     else:
@@ -319,6 +351,8 @@ def run_gpu(args):
         "config": {"workload": w.name, "M": w.M, "N": w.N, "B": w.B, "S": w.S,
                    "precision": args.precision, "rescore_topk": topk,
                    "update_warps_per_signal": chosen["update_warps"],
+                   "update_gather": "24-bit copy of A (3 bytes an element)" if args.gather24
+                   else "FP32 rows",
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "clocks": clocks,
@@ -342,6 +376,11 @@ def run_gpu(args):
                                 "kind": "oracle",
                                 "sample": f"first {n} signals of the batch, FP64 timed-mode "
                                           f"oracle, {t:.1f} s"}
+        # each result's error against the FP64 oracle, on the same signals (or more)
+        n_err = max(n, min(args.error_signals, w.B))
+        line["accuracy"] = accuracy_report(w, A, Y, n_err, chosen)
+        if plain is not None:
+            line["plain_fp32"]["accuracy"] = accuracy_report(w, A, Y, n_err, plain)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -506,6 +545,49 @@ def run_learned(args):
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t0)
     rec = lambda S_: float(np.mean([set(S_[b][S_[b] >= 0]) == set(planted[b]) for b in range(w.B)]))
+    # what the network gains over the same method without it (candidates = top-K of |A^T y|):
+    # recall of plain OMP's picks among the candidates, the fallback steps, and the time of each
+    # part (network inference alone; the candidate-restricted solve with its dense fallback)
+    K = p.desc.topk
+    cm = torch.empty((w.B, K), dtype=torch.int32, device=dev)
+    cb = torch.empty((w.B, K), dtype=torch.int32, device=dev)
+    t_infer = timed(lambda: p.infer(Ad, Yd, cm))
+    t_base_cand = timed(lambda: p.baseline_candidates(Ad, Yd, cb))
+    tau_d = torch.from_numpy(np.asarray(rep.tau, dtype=np.float32)).to(dev)
+    fb_b = torch.empty(w.B, dtype=torch.int32, device=dev)
+
+    def solve_cands(c, fbo):
+        omp.omp_solve_batch_candidates(dense.h, Ad, Yd, w.S, w.eps, c, tau_d, X, sup, n_iter, resid, fbo)
+
+    t_cand_m = timed(lambda: solve_cands(cm, fb))
+    fbm = fb.cpu().numpy()
+    t_cand_b = timed(lambda: solve_cands(cb, fb_b))
+    fbb = fb_b.cpu().numpy()
+    cm_h, cb_h = cm.cpu().numpy(), cb.cpu().numpy()
+    recall = lambda C: float(np.mean([np.isin(sup_p[b][sup_p[b] >= 0], C[b]).mean() for b in range(w.B)]))
+    # the step at which plain OMP first needs an atom that is not a candidate (S if never)
+    def first_miss(C):
+        out = np.full(w.B, w.S)
+        for b in range(w.B):
+            miss = np.flatnonzero(~np.isin(sup_p[b], C[b]) & (sup_p[b] >= 0))
+            if miss.size:
+                out[b] = miss[0]
+        return out
+    edges = list(range(0, w.S + 8, 8))
+    hist = lambda f: np.histogram(np.where(f >= 0, f, w.S), bins=edges)[0].tolist()
+    gain = {"topk": K, "tau_quantile": 1e-3,
+            "recall_of_plain_picks": {"learned": recall(cm_h), "no_network": recall(cb_h)},
+            "first_missing_pick_step_mean": {"learned": float(first_miss(cm_h).mean()),
+                                             "no_network": float(first_miss(cb_h).mean())},
+            "fallback_rate": {"learned": float(np.mean(fbm >= 0)), "no_network": float(np.mean(fbb >= 0))},
+            "mean_fallback_step": {"learned": float(np.mean(np.where(fbm >= 0, fbm, w.S))),
+                                   "no_network": float(np.mean(np.where(fbb >= 0, fbb, w.S)))},
+            "fallback_step_histogram": {"bins": edges, "learned": hist(fbm), "no_network": hist(fbb)},
+            "ms_per_solve": {"network_inference": t_infer / args.steps,
+                             "no_network_candidates": t_base_cand / args.steps,
+                             "restricted_and_fallback_learned": t_cand_m / args.steps,
+                             "restricted_and_fallback_no_network": t_cand_b / args.steps,
+                             "dense_bf16": t_dense / args.steps}}
     value = w.B * args.steps / (t_learned / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": 1, "steps": args.steps,
@@ -524,6 +606,7 @@ def run_learned(args):
                     "train_seconds_data": rep.seconds_data, "train_seconds": rep.seconds_train,
                     "train_losses": rep.losses},
         "dense_bf16": {"value": w.B * args.steps / (t_dense / 1e3), "planted_recovery": rec(sup_d)},
+        "network_gain": gain,
         "plain_fp32": {"value": w.B * args.steps / (t_plain / 1e3), "planted_recovery": rec(sup_p)},
     }
     print(json.dumps(line))
@@ -572,8 +655,13 @@ def main():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--gather24", action="store_true",
+                    help="the update gathers atom rows from the 24-bit copy of A")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--error-signals", type=int, default=0,
+                    help="signals checked against the FP64 oracle for the accuracy report "
+                         "(default: the CPU baseline's timed sample)")
     ap.add_argument("--reference-signals", type=int, default=64)
     ap.add_argument("--form", default="dense", choices=["dense", "learned", "gram"])
     ap.add_argument("--train-signals", type=int, default=1 << 20)

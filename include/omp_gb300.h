@@ -74,10 +74,16 @@ typedef struct omp_desc {
                             signal return at once), 2 with the iterations as a device-side while
                             loop that ends when no signal is live; 0: direct launches */
   int32_t device;        /* CUDA device ordinal the handle lives on */
+  int32_t gather24;      /* 1: the update's gather of the support's atom rows (q = A_S F[:,k], the
+                            residual update of Sec. 2.3) reads a 24-bit copy of A -- each element
+                            rounded to nearest at a 15-bit mantissa (relative error <= 2^-16),
+                            stored as 16 + 8 bit planes -- so 3 bytes per element move instead of
+                            4 (N x Mp x 3 more bytes of HBM). The selection, the FP32 rescoring
+                            and the factor are unchanged. 0 (default): FP32 rows. */
 } omp_desc;
 
 /* Fill `desc` with defaults for an M x N dictionary (precision BF16, rescore_topk 8,
- * eps_relative 1, use_graph 1, device 0, max_batch 4096, max_iters min(M, N, 64)). */
+ * eps_relative 1, use_graph 1, device 0, max_batch 4096, max_iters min(M, N, 64), gather24 0). */
 void omp_desc_default(omp_desc* desc, int64_t M, int64_t N);
 
 /* Create a handle: checks the device (sm_103 only), allocates every workspace for max_batch and
@@ -112,11 +118,20 @@ omp_status omp_solve_batch(omp_handle h, const float* A, const float* Y, int64_t
 /* omp_solve_batch plus per-signal diagnostics (each pointer may be NULL):
  *   n_iter_out      device, B int32: iterations performed (= number of support entries)
  *   resid_norm_out  device, B float: final ||r|| as tracked by the update (FP32 residual)
+ *   margin_out      device, B x S float: at each accepted step k the top-two score margin
+ *                   (s1 - s2) / s1 of Alg. 1's selection (1 when every other score is 0), -1 past
+ *                   the signal's last step. FP32 path: the correlation's best and runner-up over
+ *                   all atoms. Quantised paths: the FP32 scores of the rescored candidates (the
+ *                   rescore_topk best by quantised score); requesting margins makes such a solve
+ *                   rescore every candidate, with no pruning -- the same picks, more time.
  *   stop_out        device, B int32: 0 = S reached, 1 = eps, 2 = dependent atom, 3 = y == 0 or
- *                   non-finite input */
+ *                   non-finite input
+ * The margins are the selection statistic of Alg. 1 whose near-ties (margin <= 1e-3) are the
+ * only places where two correct implementations may pick different atoms. */
 omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
                               float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
-                              float* resid_norm_out, int32_t* stop_out, void* stream);
+                              float* resid_norm_out, float* margin_out, int32_t* stop_out,
+                              void* stream);
 
 /* End-to-end variant with HOST buffers for the signals and results: copies Y_host (B x M) to
  * the device, solves, copies X_host (B x S) and support_host (B x S) back and waits for the
@@ -288,6 +303,17 @@ omp_status omp_proposal_infer(omp_proposal p, const float* A, const float* Y, in
 /* Residual-drop thresholds tau[0..S) (host array). */
 omp_status omp_proposal_set_thresholds(omp_proposal p, const float* tau_host, int32_t S);
 omp_status omp_proposal_get_thresholds(omp_proposal p, float* tau_host, int32_t S);
+
+/* Save the network (FP32 master weights W1, b1, W2, b2, beta) and its residual-drop thresholds
+ * to a file, and load them back into a proposal of the same dictionary size N and hidden width.
+ * The file holds a magic tag, the shape (N, hidden, topk, S), the parameters and thresholds as
+ * little-endian FP32, and a 64-bit FNV-1a hash of all of it. Load refuses (with
+ * OMP_ERR_INVALID_ARGUMENT, nothing changed) a file that is missing, truncated, altered or of
+ * another shape; it resets the optimiser state as omp_proposal_set_weights does, and sets the
+ * thresholds the file holds (any beyond them to 0). Both synchronise the device. The paper has no
+ * learned component; these persist the proposal that restricts Alg. 1's selection. */
+omp_status omp_proposal_save(omp_proposal p, const char* path);
+omp_status omp_proposal_load(omp_proposal p, const char* path);
 
 /* tau_k = the `quantile` (e.g. 0.001) of the positive entries of column k of drops (device,
  * B x S, from omp_solve_batch_trace on labelled training signals). */

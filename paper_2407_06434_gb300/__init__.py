@@ -1,10 +1,11 @@
 """Batched Orthogonal Matching Pursuit on one GB300 (sm_103a).
 
 The compute path lives in the CUDA library ``libomp_gb300.so`` (``csrc/``) behind the C ABI of
-``include/omp_gb300.h``; ``omp`` is its Python binding (argument marshalling only) and ``build``
-compiles it in-tree.
+``include/omp_gb300.h``; ``omp`` is its Python binding (argument marshalling only), ``estimator`` a
+scikit-learn-style front end on top of it, and ``build`` compiles the library in-tree.
 """
-from . import build, omp  # noqa: F401
+from . import build, estimator, omp  # noqa: F401
+from .estimator import OrthogonalMatchingPursuit, orthogonal_mp  # noqa: F401
 from .omp import (  # noqa: F401
     OmpError,
     OmpSolver,

@@ -10,7 +10,9 @@
 //   delta = ||a_{n*}||^2 - ||z||^2 in FP64; the atom is dependent if delta <= 1e-10 ||a_{n*}||^2
 //   gamma = 1 / sqrt(delta)       FP64: the diagonal of the new inverse-Cholesky column
 //   F[:,k] = [-gamma F_k z ; gamma]  (stored in FP64 and FP32)
-//   q     = A_{S+n*} F[:,k]       the new orthonormal direction (FP32 gather of k+1 atom rows)
+//   q     = A_{S+n*} F[:,k]       the new orthonormal direction (gather of k+1 atom rows: FP32, or
+//                                  with the handle's 24-bit option the rows rounded to a 15-bit
+//                                  mantissa, read as 3 bytes per element)
 //   b_k   = q^T r,  r <- r - b_k q (y_hat = A_k F_k (A_k F_k)^T y built one term at a time)
 // and, with one warp per signal, the next step's quantised operand row at this position, and
 // (BF16) the next correlation's pruning threshold from the exact FP32 correlation of the new
@@ -206,7 +208,58 @@ __device__ __forceinline__ void append_column(const Ws& ws, const GroupSmem& gs,
   }
 }
 
-template <int W, int V>
+// Four consecutive elements of an atom row (float4 slot s) for the q gather: from the FP32 rows,
+// or (G24) rebuilt from the 24-bit split copy -- 8 bytes of high halves and 4 bytes of the next
+// 8 bits, i.e. the element rounded to a 15-bit mantissa, three quarters of the FP32 bytes.
+// The loaded words stay in their raw form (3 registers for G24) while the rows are in flight and
+// are widened only where they are multiplied.
+template <bool G24>
+struct Slot4 {
+  float4 v;
+};
+template <>
+struct Slot4<true> {
+  uint2 h;
+  uint32_t l;
+};
+
+template <bool G24>
+__device__ __forceinline__ Slot4<G24> gather4(const Ws& ws, int n, int s) {
+  Slot4<G24> r;
+  if constexpr (G24) {
+    r.h = __ldg(reinterpret_cast<const uint2*>(ws.A24h + static_cast<size_t>(n) * ws.Mp) + s);
+    r.l = __ldg(reinterpret_cast<const uint32_t*>(ws.A24l + static_cast<size_t>(n) * ws.Mp) + s);
+  } else {
+    r.v = __ldg(reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n) * ws.Mp) + s);
+  }
+  return r;
+}
+template <bool G24>
+__device__ __forceinline__ Slot4<G24> zero4() {
+  Slot4<G24> r;
+  if constexpr (G24) {
+    r.h = make_uint2(0u, 0u);
+    r.l = 0u;
+  } else {
+    r.v = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  return r;
+}
+template <bool G24>
+__device__ __forceinline__ float4 widen(const Slot4<G24>& r) {
+  if constexpr (G24) {
+    float4 v;
+    v.x = __uint_as_float((r.h.x << 16) | ((r.l & 0xFFu) << 8));
+    v.y = __uint_as_float((r.h.x & 0xFFFF0000u) | (((r.l >> 8) & 0xFFu) << 8));
+    v.z = __uint_as_float((r.h.y << 16) | (((r.l >> 16) & 0xFFu) << 8));
+    v.w = __uint_as_float((r.h.y & 0xFFFF0000u) | ((r.l >> 24) << 8));
+    return v;
+  } else {
+    return r.v;
+  }
+}
+
+template <int W, int V, bool G24>
 __global__ void __launch_bounds__(W * 32, 16 / W)
     append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
   k = iter_of(ws, k);
@@ -256,8 +309,15 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   }
   const float rprev = ws.rnorm[id];
   const float ynorm = ws.ynorm[id];
-  // the pruning threshold the correlation used for this position (0: none)
+  // the pruning threshold the correlation used for this position (0: none; in the units of the
+  // quantised scores) and this step's score error bound per unit of ||r||: the one the previous
+  // step derived from this residual row's actual quantisation error, else the worst case
   const float tau_used = ws.tau_pos ? ws.tau_pos[p] : 0.f;
+  float eps_k = ws.rescore_eps;
+  if (ws.tau && ws.rescore_eps > 0.f) {
+    const TauRec tr = ws.tau[id];
+    if (tr.step == k && tr.eps > 0.f) eps_k = fminf(tr.eps, ws.rescore_eps);
+  }
 
   const int M4 = ws.Mp >> 2;
   const float4* rrow = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
@@ -285,7 +345,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       // leave out the residual's scale qs, so the window is taken in their units.
       const float qs = ws.prec == OMP_PREC_FP8_E4M3 ? ws.sr[k & 1][p] : 1.f;
       const bool bound = ws.rescore_eps > 0.f && rprev > 1e-30f && qs > 0.f;
-      const float win = bound ? 2.f * ws.rescore_eps * rprev / qs : 0.f;
+      const float win = bound ? 2.f * eps_k * rprev / qs : 0.f;
       float s_first = 0.f;
       int nres = ws.topk;
       for (int sel = 0; sel < ws.topk; ++sel) {
@@ -329,6 +389,9 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
           break;
         }
       }
+      // margins recorded: at least the two best are rescored (the handle then runs without
+      // the score bound, so nothing is skipped or trimmed)
+      if (ws.margin && nres < 2 && ws.topk >= 2) nres = 2;
       if (lane == 0) gs.scal[3] = nres;
       // The rescoring can only confirm the quantised best when its lead over the second is
       // more than twice the bound on |quantised - FP32| score (rescore_eps ||r||, from the
@@ -399,6 +462,8 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         ix = gs.cidx[lane];
         sc = fabsf(v) * __ldg(ws.inv_norm + ix);
       }
+      const float own_s = sc;
+      const int own_i = ix;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float os = __shfl_xor_sync(0xffffffffu, sc, o);
@@ -409,6 +474,10 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         }
       }
       if (lane == 0) gs.scal[0] = ix;
+      if (ws.margin) {  // (s1 - s2) / s1 over the FP32 scores of the rescored candidates
+        const float s2 = warp_max(own_i != ix ? own_s : -2.f);
+        if (lane == 0) gs.top2[1] = sc > 0.f ? (s2 > 0.f ? (sc - s2) / sc : 1.f) : 0.f;
+      }
     }
     group_sync(W, grp);
     ns = gs.scal[0];
@@ -458,51 +527,50 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   // row in flight
   for (; a + 3 <= na; a += 3) {
     const float f0 = gs.f[a], f1 = gs.f[a + 1], f2 = gs.f[a + 2];
-    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
-    const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 1]) * ws.Mp);
-    const float4* a2 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 2]) * ws.Mp);
-    float4 v0[V], v1[V], v2[V];
+    const int n0 = gs.sup[a], n1 = gs.sup[a + 1], n2 = gs.sup[a + 2];
+    Slot4<G24> w0[V], w1[V], w2[V];
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int s = t * (W * 32) + wig * 32 + lane;
-      v0[t] = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v1[t] = s < M4 ? __ldg(a1 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v2[t] = s < M4 ? __ldg(a2 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w0[t] = s < M4 ? gather4<G24>(ws, n0, s) : zero4<G24>();
+      w1[t] = s < M4 ? gather4<G24>(ws, n1, s) : zero4<G24>();
+      w2[t] = s < M4 ? gather4<G24>(ws, n2, s) : zero4<G24>();
     }
 #pragma unroll
     for (int t = 0; t < V; ++t) {
-      q[t].x = fmaf(f2, v2[t].x, fmaf(f1, v1[t].x, fmaf(f0, v0[t].x, q[t].x)));
-      q[t].y = fmaf(f2, v2[t].y, fmaf(f1, v1[t].y, fmaf(f0, v0[t].y, q[t].y)));
-      q[t].z = fmaf(f2, v2[t].z, fmaf(f1, v1[t].z, fmaf(f0, v0[t].z, q[t].z)));
-      q[t].w = fmaf(f2, v2[t].w, fmaf(f1, v1[t].w, fmaf(f0, v0[t].w, q[t].w)));
+      const float4 v0 = widen<G24>(w0[t]), v1 = widen<G24>(w1[t]), v2 = widen<G24>(w2[t]);
+      q[t].x = fmaf(f2, v2.x, fmaf(f1, v1.x, fmaf(f0, v0.x, q[t].x)));
+      q[t].y = fmaf(f2, v2.y, fmaf(f1, v1.y, fmaf(f0, v0.y, q[t].y)));
+      q[t].z = fmaf(f2, v2.z, fmaf(f1, v1.z, fmaf(f0, v0.z, q[t].z)));
+      q[t].w = fmaf(f2, v2.w, fmaf(f1, v1.w, fmaf(f0, v0.w, q[t].w)));
     }
   }
   for (; a + 2 <= na; a += 2) {
     const float f0 = gs.f[a], f1 = gs.f[a + 1];
-    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
-    const float4* a1 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a + 1]) * ws.Mp);
-    float4 v0[V], v1[V];
+    const int n0 = gs.sup[a], n1 = gs.sup[a + 1];
+    Slot4<G24> w0[V], w1[V];
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int s = t * (W * 32) + wig * 32 + lane;
-      v0[t] = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v1[t] = s < M4 ? __ldg(a1 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w0[t] = s < M4 ? gather4<G24>(ws, n0, s) : zero4<G24>();
+      w1[t] = s < M4 ? gather4<G24>(ws, n1, s) : zero4<G24>();
     }
 #pragma unroll
     for (int t = 0; t < V; ++t) {
-      q[t].x = fmaf(f1, v1[t].x, fmaf(f0, v0[t].x, q[t].x));
-      q[t].y = fmaf(f1, v1[t].y, fmaf(f0, v0[t].y, q[t].y));
-      q[t].z = fmaf(f1, v1[t].z, fmaf(f0, v0[t].z, q[t].z));
-      q[t].w = fmaf(f1, v1[t].w, fmaf(f0, v0[t].w, q[t].w));
+      const float4 v0 = widen<G24>(w0[t]), v1 = widen<G24>(w1[t]);
+      q[t].x = fmaf(f1, v1.x, fmaf(f0, v0.x, q[t].x));
+      q[t].y = fmaf(f1, v1.y, fmaf(f0, v0.y, q[t].y));
+      q[t].z = fmaf(f1, v1.z, fmaf(f0, v0.z, q[t].z));
+      q[t].w = fmaf(f1, v1.w, fmaf(f0, v0.w, q[t].w));
     }
   }
   if (a < na) {
     const float f0 = gs.f[a];
-    const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(gs.sup[a]) * ws.Mp);
+    const int n0 = gs.sup[a];
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int s = t * (W * 32) + wig * 32 + lane;
-      const float4 v = s < M4 ? __ldg(a0 + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = widen<G24>(s < M4 ? gather4<G24>(ws, n0, s) : zero4<G24>());
       q[t].x = fmaf(f0, v.x, q[t].x);
       q[t].y = fmaf(f0, v.y, q[t].y);
       q[t].z = fmaf(f0, v.z, q[t].z);
@@ -560,11 +628,14 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       gs.cpart[2 * wig + 1] = d1;
     }
   }
+  float qe2 = -1.f;  // squared norm of the next row's quantisation error (W == 1; -1: not known)
   if (W == 1 && !top1) {
     // The next step's quantised operand row, at this position: the compaction keeps it where
     // no signal before this one retired, and re-quantises from R32 otherwise. Same rounding as
     // the compaction's (BF16 round-to-nearest-even; E4M3 satfinite with the row's amax / 448).
+    // The squared norm of its rounding error feeds the next step's data-driven score bound.
     const int j = (k + 1) & 1;
+    float e2 = 0.f;
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat162* dq = reinterpret_cast<__nv_bfloat162*>(
           static_cast<__nv_bfloat16*>(ws.Rq[j]) + static_cast<size_t>(p) * ws.Mp);
@@ -572,8 +643,13 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       for (int t = 0; t < V; ++t) {
         const int s = t * 32 + lane;
         if (s < M4) {
-          dq[2 * s] = __floats2bfloat162_rn(r[t].x, r[t].y);
-          dq[2 * s + 1] = __floats2bfloat162_rn(r[t].z, r[t].w);
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(r[t].x, r[t].y);
+          const __nv_bfloat162 h1 = __floats2bfloat162_rn(r[t].z, r[t].w);
+          dq[2 * s] = h0;
+          dq[2 * s + 1] = h1;
+          const float2 g0 = __bfloat1622float2(h0), g1 = __bfloat1622float2(h1);
+          const float d0 = g0.x - r[t].x, d1 = g0.y - r[t].y, d2 = g1.x - r[t].z, d3 = g1.y - r[t].w;
+          e2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
         }
       }
     } else {
@@ -587,19 +663,29 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       amax = warp_max(amax);
       const float inv = amax > 0.f ? 448.f / amax : 0.f;
       if (lane == 0) ws.sr[j][p] = amax > 0.f ? amax / 448.f : 0.f;
+      const float sr = amax > 0.f ? amax / 448.f : 0.f;
       uint32_t* dq = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws.Rq[j]) + static_cast<size_t>(p) * ws.Mp);
 #pragma unroll
       for (int t = 0; t < V; ++t) {
         const int s = t * 32 + lane;
         if (s < M4) {
-          const uint32_t b0 = __nv_cvt_float_to_fp8(r[t].x * inv, __NV_SATFINITE, __NV_E4M3);
-          const uint32_t b1 = __nv_cvt_float_to_fp8(r[t].y * inv, __NV_SATFINITE, __NV_E4M3);
-          const uint32_t b2 = __nv_cvt_float_to_fp8(r[t].z * inv, __NV_SATFINITE, __NV_E4M3);
-          const uint32_t b3 = __nv_cvt_float_to_fp8(r[t].w * inv, __NV_SATFINITE, __NV_E4M3);
-          dq[s] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+          const __nv_fp8_storage_t b0 = __nv_cvt_float_to_fp8(r[t].x * inv, __NV_SATFINITE, __NV_E4M3);
+          const __nv_fp8_storage_t b1 = __nv_cvt_float_to_fp8(r[t].y * inv, __NV_SATFINITE, __NV_E4M3);
+          const __nv_fp8_storage_t b2 = __nv_cvt_float_to_fp8(r[t].z * inv, __NV_SATFINITE, __NV_E4M3);
+          const __nv_fp8_storage_t b3 = __nv_cvt_float_to_fp8(r[t].w * inv, __NV_SATFINITE, __NV_E4M3);
+          dq[s] = static_cast<uint32_t>(b0) | (static_cast<uint32_t>(b1) << 8) |
+                  (static_cast<uint32_t>(b2) << 16) | (static_cast<uint32_t>(b3) << 24);
+          if (ws.tau) {
+            const float d0 = fmaf(e4m3_to_float(b0), sr, -r[t].x);
+            const float d1 = fmaf(e4m3_to_float(b1), sr, -r[t].y);
+            const float d2 = fmaf(e4m3_to_float(b2), sr, -r[t].z);
+            const float d3 = fmaf(e4m3_to_float(b3), sr, -r[t].w);
+            e2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+          }
         }
       }
     }
+    qe2 = warp_sum_f(e2);
   }
   if (lane == 0) pf[8 + wig] = rr;
   group_sync(W, grp);
@@ -612,6 +698,17 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     ws.bv[static_cast<size_t>(id) * ws.Smax + kk] = static_cast<double>(bf);
     ws.sup[static_cast<size_t>(id) * ws.Smax + kk] = ns;
     ws.drop[static_cast<size_t>(id) * ws.Smax + kk] = rprev > 0.f ? (bf / rprev) * (bf / rprev) : 0.f;
+    if (ws.margin) {
+      float mg;
+      if (top1) {  // the correlation's best and runner-up keys (FP32 scores)
+        const unsigned long long k2 = ws.cand2[p];
+        const float s1 = key_score(ws.cand1[p]), s2 = k2 ? key_score(k2) : 0.f;
+        mg = s1 > 0.f ? (s1 - s2) / s1 : 0.f;
+      } else {
+        mg = gs.top2[1];
+      }
+      ws.margin[static_cast<size_t>(id) * ws.Smax + kk] = mg;
+    }
     ws.niter[id] = kk + 1;
     ws.rnorm[id] = rn;
     const float thr = eps_rel ? eps * ynorm : eps;
@@ -643,9 +740,16 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       for (int w = 0; w < W; ++w) d += gs.cpart[2 * w + c];
       best = fmaxf(best, fabsf(d) * gs.rinv[c]);
     }
+    // the next step's bound: from the next row's actual quantisation error when this block
+    // quantised it (one warp per signal), else the worst case
+    float eps_n = ws.rescore_eps;
+    if (qe2 >= 0.f && rk > 0.f) {
+      const float er = sqrtf(qe2) / rk * (1.f + 0x1p-20f);
+      eps_n = fminf(eps_n, data_bound(ws, *ws.ea, er));
+    }
     const float lb = best * (1.f - 0x1p-20f) - static_cast<float>(ws.Mp) * 0x1p-23f * rk;
-    const float tau = lb - 3.f * ws.rescore_eps * rk;
-    ws.tau[id] = TauRec{tau > 0.f ? tau : 0.f, k + 1};
+    const float tau = lb - 3.f * eps_n * rk;
+    ws.tau[id] = TauRec{tau > 0.f ? tau : 0.f, eps_n, k + 1, 0};
   }
 }
 
@@ -653,7 +757,10 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
 template <int W, int V>
 void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
   const size_t smem = group_bytes(ws);
-  append_update_kernel<W, V><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
+  if (ws.A24h)
+    append_update_kernel<W, V, true><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
+  else
+    append_update_kernel<W, V, false><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
 }
 
 template <int W>
@@ -666,7 +773,8 @@ void launch_w(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, 
 
 template <int W, int V>
 cudaError_t set_attr_t(int bytes) {
-  return raise_smem_limit(reinterpret_cast<const void*>(append_update_kernel<W, V>), bytes);
+  const cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(append_update_kernel<W, V, false>), bytes);
+  return e != cudaSuccess ? e : raise_smem_limit(reinterpret_cast<const void*>(append_update_kernel<W, V, true>), bytes);
 }
 
 template <int W>

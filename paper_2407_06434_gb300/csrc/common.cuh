@@ -3,6 +3,8 @@
 // Data layout in HBM (one handle):
 //   dictionary (prepared once per A):
 //     A32   N x Mp  float   atom rows, zero padded to Mp (64; 128 for E4M3) -- update / rescoring
+//     A24h  N x Mp  u16     optional 24-bit copy for the update's q gather: each element rounded
+//     A24l  N x Mp  u8      to nearest at 24 bits, split into its high 16 and next 8 bits
 //     A16   N x Mp  bf16    RN-even copy                                     -- BF16 correlation
 //     A8    N x Mp  e4m3    per-atom scaled copy, sa[n] = amax_n / 448        -- FP8 correlation
 //     inv_norm[N] float = 1/||a_n|| (from FP64), norm2[N] double = ||a_n||^2
@@ -21,6 +23,8 @@
 //     Rq[2]          Bpad x Mp quantised residual rows in position order (tensor-core operand)
 //     sr[2][Bpad]    per-position FP8 scale of Rq
 //     cand1[Bmax]    FP32 path: packed (score, ~index) key, merged with atomicMax
+//     cand2[Bmax]    FP32 path, margins recorded: the runner-up's key (every key that loses a
+//                    merge, and each tile's own second best, is merged into it)
 //     cand_s/cand_i  quantised paths: per position, candidate pieces x 8 (score, index)
 #pragma once
 #include <cuda_runtime.h>
@@ -41,10 +45,13 @@ constexpr int kTcParts = 2;           // candidate lists per signal and correlat
 constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a||^2
 constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
 
-// BF16 path: a signal's pruning threshold for the correlation of step `step` (see append.cu)
-struct alignas(8) TauRec {
+// Quantised paths: a signal's pruning threshold for the correlation of step `step` and the score
+// error bound (per unit of ||r||) of that step's quantised residual (see append.cu)
+struct alignas(16) TauRec {
   float tau;
+  float eps;
   int step;
+  int pad;
 };
 
 struct Ws {
@@ -59,6 +66,8 @@ struct Ws {
   int64_t Fstride; // Smax (Smax + 1) / 2 rounded up to a multiple of 4
   // dictionary
   float* A32;
+  uint16_t* A24h;  // 24-bit gather copy (optional): the high 16 bits of each element rounded to
+  uint8_t* A24l;   // 24 bits (sign, exponent, 15 mantissa bits), and the next 8 bits
   __nv_bfloat16* A16;
   uint8_t* A8;
   float* sa;
@@ -75,7 +84,9 @@ struct Ws {
   int* cnt;
   int* kdev;       // iteration counter of the graph's device-side loop
   float rescore_eps;  // bound on |quantised score - FP32 score| per unit of ||r|| (0: none)
-  TauRec* tau;     // BF16 with the rescoring bound: per signal, next step's pruning threshold
+  float* ea;       // quantised paths: max over atoms of ||q(a_n) - a_n|| / ||a_n|| (device scalar)
+  float gam_tc, gam_32;  // accumulation bounds over Mp terms: tensor core and FP32 rescoring
+  TauRec* tau;     // quantised paths with the bound: per signal, next step's threshold and bound
   float* tau_pos;  // the same per live position of the current step (0: no pruning); or null
   uint8_t* flag;
   unsigned long long* cand1;
@@ -90,6 +101,9 @@ struct Ws {
   int* niter;
   int* stop;
   float* drop;     // Bmax x Smax: normalised residual drop b_k^2 / ||r_{k-1}||^2 of each step
+  float* margin;   // Bmax x Smax: top-two score margin (s1 - s2) / s1 of each step; null unless
+                   // the solve records it (then the quantised paths rescore every candidate)
+  unsigned long long* cand2;  // FP32 path with margins: the runner-up's packed key per position
   int* fb;         // Bmax: learned solve, step at which the signal left the restricted phase
   unsigned int* err;
 };
@@ -106,6 +120,7 @@ struct CallArgs {
   int* topk_idx;     // omp_correlate_topk outputs
   float* topk_score;
   float* drop;       // optional B x S trace of normalised residual drops
+  float* margin;     // optional B x S trace of top-two score margins
   int* fallback;     // optional B: learned solve fallback step (-1 = none)
 };
 
@@ -124,6 +139,19 @@ __device__ __forceinline__ float key_score(unsigned long long key) {
 // (s, i) beats (t, j): higher score, or equal score and lower index
 __device__ __forceinline__ bool better(float s, int i, float t, int j) {
   return s > t || (s == t && i < j);
+}
+
+// value of an E4M3 code (the conversion intrinsic through half precision, which holds it exactly)
+__device__ __forceinline__ float e4m3_to_float(__nv_fp8_storage_t c) {
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
+}
+
+// The score error bound of one step, per unit of ||a|| ||r||, from the actual relative
+// quantisation errors of the atoms (ea, at most) and of the residual row (er): by Cauchy-Schwarz
+// |<q(a), q(r)> - <a, r>| <= (ea + er + ea er) ||a|| ||r||, plus the tensor-core and the FP32
+// rescoring accumulations, and 1% for the rounding of the norms, scales and of this bound.
+__device__ __forceinline__ float data_bound(const Ws& ws, float ea, float er) {
+  return 1.01f * (ea + er + ea * er + (1.f + ea) * (1.f + er) * ws.gam_tc + ws.gam_32);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

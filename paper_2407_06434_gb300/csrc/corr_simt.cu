@@ -148,6 +148,60 @@ __global__ void __launch_bounds__(256, 2) simt_tile_kernel(Ws ws, int k) {
   float inv[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) inv[j] = ncol[j] < ws.N ? __ldg(ws.inv_norm + ncol[j]) : 0.f;
+  if (ws.cand2) {
+    // Margins recorded: each row's best two atoms of the tile (same scan and ties), then
+    // cand1 keeps the global best as before and cand2 receives every key that loses a merge
+    // (the smaller of the old and the new key of each atomicMax) and each tile's second best,
+    // so that it ends with the largest key other than the best: the runner-up.
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int prow = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+      float b1 = -1.f, b2 = -1.f;
+      int i1 = 0x7fffffff, i2 = 0x7fffffff;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (ncol[j] < ws.N) {
+          const float sc = fabsf(acc[i][j]) * inv[j];
+          if (better(sc, ncol[j], b1, i1)) {
+            b2 = b1;
+            i2 = i1;
+            b1 = sc;
+            i1 = ncol[j];
+          } else if (better(sc, ncol[j], b2, i2)) {
+            b2 = sc;
+            i2 = ncol[j];
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const float o1 = __shfl_xor_sync(0xffffffffu, b1, o);
+        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+        const float o2 = __shfl_xor_sync(0xffffffffu, b2, o);
+        const int oi2 = __shfl_xor_sync(0xffffffffu, i2, o);
+        if (better(o1, oi1, b1, i1)) {
+          if (!better(b1, i1, o2, oi2)) {
+            b1 = o2;  // the partner holds both: (o1, o2)
+            i1 = oi2;
+          }
+          b2 = b1;
+          i2 = i1;
+          b1 = o1;
+          i1 = oi1;
+        } else if (better(o1, oi1, b2, i2)) {
+          b2 = o1;
+          i2 = oi1;
+        }
+      }
+      if (tx == 0 && prow < L && i1 < ws.N) {
+        const unsigned long long k1 = pack_key(b1, i1);
+        const unsigned long long old = atomicMax(ws.cand1 + prow, k1);
+        atomicMax(ws.cand2 + prow, old < k1 ? old : k1);
+        if (i2 < ws.N) atomicMax(ws.cand2 + prow, pack_key(b2, i2));
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int prow = p0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));

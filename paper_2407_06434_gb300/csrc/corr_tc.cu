@@ -14,10 +14,9 @@
 // EPI_PARTS (g - owner(s * Tn)) + part, so a tile's lists occupy consecutive slots; the
 // mainloop's minimum units per CTA (`cmin`) bounds the pieces per tile by kPieces / EPI_PARTS.
 //
-// On the BF16 path each row may carry a pruning threshold from the previous step's update (a
-// lower bound on its best score less three score error bounds, see append.cu): columns at or
-// below it are not inserted, which removes most of the insertion work once the solve is past
-// its first step.
+// Each row may carry a pruning threshold from the previous step's update (a lower bound on its
+// best score less three score error bounds, see append.cu): columns at or below it are not
+// inserted, which removes most of the insertion work once the solve is past its first step.
 #include "tcgemm.cuh"
 
 namespace ompk {
@@ -78,11 +77,11 @@ using namespace tcg;
 // smaller and only prunes less; a value tagged with another tile is ignored.
 template <int PREC>
 struct EpiTop8 {
-  // BF16 rows may be pruned by a threshold; each list then also keeps its running best column
+  // Rows may be pruned by a threshold; each list then also keeps its running best column
   // as a key (score bits with the low 5 mantissa bits replaced by 31 - the column's place in its
   // chunk, so that an integer max takes the higher score and, within 2^-18, the lower index) and
   // emits it if nothing passed the threshold, so the merged lists always offer a runner-up
-  static constexpr bool kTrack = PREC == OMP_PREC_BF16;
+  static constexpr bool kTrack = true;
   Ws ws;
   int L;
   int g, T, Geff, row, part, cur_s;
@@ -126,8 +125,8 @@ struct EpiTop8 {
     }
   }
   // The update kernel's lower bound on the row's best score, less three score error bounds
-  // (written per live position by the compaction); a column at or below it can be neither the
-  // pick nor a rescoring candidate that changes it. BF16 path only.
+  // (written per live position by the compaction, in the units of the scores); a column at or
+  // below it can be neither the pick nor a rescoring candidate that changes it.
   __device__ float load_tau(int s) const {
     const int p = s * BM + row;
     if (!ws.tau_pos || p >= L) return -1.f;

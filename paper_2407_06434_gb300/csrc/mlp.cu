@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "tcgemm.cuh"
@@ -853,6 +854,107 @@ omp_status omp_proposal_get_thresholds(omp_proposal p, float* tau_host, int32_t 
   return cudaMemcpy(tau_host, p->tau, static_cast<size_t>(S) * 4, cudaMemcpyDeviceToHost) == cudaSuccess
              ? OMP_OK
              : OMP_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------------------ save / load
+// File layout (little-endian): the 8 bytes "OMPPROP1"; int32 N, hidden, topk, S (thresholds);
+// FP32 W1 (hidden x N), b1 (hidden), W2 (N x hidden), b2 (N), beta (1), tau (S); then a 64-bit
+// FNV-1a hash of every byte before it, so a truncated or altered file is refused.
+namespace {
+constexpr char kPropMagic[8] = {'O', 'M', 'P', 'P', 'R', 'O', 'P', '1'};
+
+uint64_t fnv1a(const unsigned char* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= data[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct PropFile {
+  int32_t hdr[4];  // N, hidden, topk, S
+  std::vector<float> W1, b1, W2, b2, beta, tau;
+};
+
+size_t prop_payload_floats(const int32_t* hdr) {
+  const size_t N = static_cast<size_t>(hdr[0]), H = static_cast<size_t>(hdr[1]);
+  return 2 * N * H + H + N + 1 + static_cast<size_t>(hdr[3]);
+}
+}  // namespace
+
+omp_status omp_proposal_save(omp_proposal p, const char* path) {
+  if (!p || !path) return OMP_ERR_INVALID_ARGUMENT;
+  const int32_t hdr[4] = {p->N, p->H, p->d.topk, p->Smax_tau};
+  const size_t n1 = static_cast<size_t>(p->H) * p->N;
+  std::vector<float> buf(prop_payload_floats(hdr));
+  float* W1 = buf.data();
+  float* W2 = W1 + n1;
+  float* b1 = W2 + n1;
+  float* b2 = b1 + p->H;
+  float* beta = b2 + p->N;
+  float* tau = beta + 1;
+  omp_status st = omp_proposal_get_weights(p, W1, b1, W2, b2, beta, nullptr);
+  if (st == OMP_OK) st = omp_proposal_get_thresholds(p, tau, p->Smax_tau);
+  if (st != OMP_OK) return st;
+  // written in the file's order: W1, b1, W2, b2, beta, tau
+  std::vector<unsigned char> out(sizeof(kPropMagic) + sizeof(hdr) + buf.size() * 4);
+  unsigned char* o = out.data();
+  std::memcpy(o, kPropMagic, sizeof(kPropMagic));
+  o += sizeof(kPropMagic);
+  std::memcpy(o, hdr, sizeof(hdr));
+  o += sizeof(hdr);
+  const std::pair<const float*, size_t> parts[] = {{W1, n1}, {b1, static_cast<size_t>(p->H)}, {W2, n1},
+                                                   {b2, static_cast<size_t>(p->N)}, {beta, 1},
+                                                   {tau, static_cast<size_t>(p->Smax_tau)}};
+  for (const auto& part : parts) {
+    std::memcpy(o, part.first, part.second * 4);
+    o += part.second * 4;
+  }
+  const uint64_t h = fnv1a(out.data(), out.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return OMP_ERR_INVALID_ARGUMENT;
+  const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size() &&
+                  std::fwrite(&h, sizeof(h), 1, f) == 1;
+  return (std::fclose(f) == 0 && ok) ? OMP_OK : OMP_ERR_INVALID_ARGUMENT;
+}
+
+omp_status omp_proposal_load(omp_proposal p, const char* path) {
+  if (!p || !path) return OMP_ERR_INVALID_ARGUMENT;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return OMP_ERR_INVALID_ARGUMENT;
+  std::vector<unsigned char> in;
+  unsigned char chunk[1 << 16];
+  size_t got;
+  while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) in.insert(in.end(), chunk, chunk + got);
+  std::fclose(f);
+  const size_t head = sizeof(kPropMagic) + 4 * sizeof(int32_t);
+  if (in.size() < head + sizeof(uint64_t) || std::memcmp(in.data(), kPropMagic, sizeof(kPropMagic)) != 0)
+    return OMP_ERR_INVALID_ARGUMENT;
+  int32_t hdr[4];
+  std::memcpy(hdr, in.data() + sizeof(kPropMagic), sizeof(hdr));
+  if (hdr[0] != p->N || hdr[1] != p->H || hdr[3] < 1 || hdr[3] > 4096) return OMP_ERR_INVALID_ARGUMENT;
+  const size_t nf = prop_payload_floats(hdr);
+  if (in.size() != head + nf * 4 + sizeof(uint64_t)) return OMP_ERR_INVALID_ARGUMENT;
+  uint64_t h = 0;
+  std::memcpy(&h, in.data() + head + nf * 4, sizeof(h));
+  if (h != fnv1a(in.data(), head + nf * 4)) return OMP_ERR_INVALID_ARGUMENT;
+  std::vector<float> buf(nf);
+  std::memcpy(buf.data(), in.data() + head, nf * 4);
+  const size_t n1 = static_cast<size_t>(p->H) * p->N;
+  const float* W1 = buf.data();
+  const float* b1 = W1 + n1;
+  const float* W2 = b1 + p->H;
+  const float* b2 = W2 + n1;
+  const float* beta = b2 + p->N;
+  const float* tau = beta + 1;
+  omp_status st = omp_proposal_set_weights(p, W1, b1, W2, b2, beta, nullptr);
+  if (st == OMP_OK && cudaDeviceSynchronize() != cudaSuccess) st = OMP_ERR_CUDA;
+  // thresholds: as many as both the file and the proposal hold; the rest accept every step
+  const int S = hdr[3] < p->Smax_tau ? hdr[3] : p->Smax_tau;
+  std::vector<float> t(static_cast<size_t>(p->Smax_tau), 0.f);
+  std::memcpy(t.data(), tau, static_cast<size_t>(S) * 4);
+  if (st == OMP_OK) st = omp_proposal_set_thresholds(p, t.data(), p->Smax_tau);
+  return st;
 }
 
 omp_status omp_proposal_calibrate(omp_proposal p, const float* drops, int64_t B, int32_t S, float quantile,

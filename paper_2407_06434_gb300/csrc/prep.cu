@@ -1,7 +1,8 @@
 // Dictionary preparation (once per A): FP64 column norms (the ||a_n|| of Alg. 1's score, App. A),
-// the zero-padded FP32 atom rows used by the update, and the quantised copies used by the
-// tensor-core correlation (BF16 round-to-nearest-even; E4M3 with a per-atom scale
-// amax_n / 448, satfinite round-to-nearest-even).
+// the zero-padded FP32 atom rows used by the update, the optional 24-bit split copy of them for
+// the update's q gather, and the quantised copies used by the tensor-core correlation (BF16
+// round-to-nearest-even; E4M3 with a per-atom scale amax_n / 448, satfinite
+// round-to-nearest-even).
 #include "common.cuh"
 
 namespace ompk {
@@ -32,15 +33,47 @@ __global__ void __launch_bounds__(256) prep_kernel(Ws ws, const float* __restric
       const float in = s > 0.0 ? static_cast<float>(1.0 / sqrt(s)) : 0.f;
       ws.escale[n] = ws.prec == OMP_PREC_FP8_E4M3 ? (amax > 0.f ? amax / 448.f : 0.f) * in : in;
     }
+    if (ws.A24h) {
+      // round to nearest (ties to even) at the 8th bit, then split: the value rebuilt from the two
+      // planes is a with its mantissa rounded to 15 bits (relative error <= 2^-16)
+      uint16_t* h = ws.A24h + static_cast<size_t>(n) * ws.Mp;
+      uint8_t* l = ws.A24l + static_cast<size_t>(n) * ws.Mp;
+      for (int m = lane; m < ws.Mp; m += 32) {
+        const uint32_t u = __float_as_uint(a32[m]);
+        const uint32_t r = u + 0x7Fu + ((u >> 8) & 1u);
+        h[m] = static_cast<uint16_t>(r >> 16);
+        l[m] = static_cast<uint8_t>(r >> 8);
+      }
+    }
+    // e2: squared norm of the quantisation error of the atom as the correlation sees it (the BF16
+    // value, or the E4M3 code times the atom's scale), for the data-driven score bound
+    double e2 = 0.0;
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat16* a16 = ws.A16 + static_cast<size_t>(n) * ws.Mp;
-      for (int m = lane; m < ws.Mp; m += 32) a16[m] = __float2bfloat16_rn(a32[m]);
+      for (int m = lane; m < ws.Mp; m += 32) {
+        const __nv_bfloat16 q = __float2bfloat16_rn(a32[m]);
+        a16[m] = q;
+        const double d = static_cast<double>(__bfloat162float(q)) - static_cast<double>(a32[m]);
+        e2 += d * d;
+      }
     } else if (ws.prec == OMP_PREC_FP8_E4M3) {
       const float inv = amax > 0.f ? 448.f / amax : 0.f;
-      if (lane == 0) ws.sa[n] = amax > 0.f ? amax / 448.f : 0.f;
+      const float sa = amax > 0.f ? amax / 448.f : 0.f;
+      if (lane == 0) ws.sa[n] = sa;
       uint8_t* a8 = ws.A8 + static_cast<size_t>(n) * ws.Mp;
-      for (int m = lane; m < ws.Mp; m += 32)
-        a8[m] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(a32[m] * inv, __NV_SATFINITE, __NV_E4M3));
+      for (int m = lane; m < ws.Mp; m += 32) {
+        const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(a32[m] * inv, __NV_SATFINITE, __NV_E4M3);
+        a8[m] = static_cast<uint8_t>(c);
+        const double d = static_cast<double>(e4m3_to_float(c)) * sa - static_cast<double>(a32[m]);
+        e2 += d * d;
+      }
+    }
+    if (ws.ea) {
+      e2 = warp_sum(e2);
+      if (lane == 0 && s > 0.0) {
+        const float rel = static_cast<float>(sqrt(e2 / s)) * (1.f + 0x1p-20f);
+        atomicMax(reinterpret_cast<unsigned int*>(ws.ea), __float_as_uint(rel));
+      }
     }
   }
 }

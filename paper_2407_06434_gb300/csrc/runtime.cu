@@ -20,7 +20,8 @@ using namespace ompk;
 struct GraphEntry {
   int B, S;
   float eps;
-  int prof;  // 1 if captured with profiling event nodes
+  int prof;   // 1 if captured with profiling event nodes
+  int stats;  // 1 if captured with the per-step margins recorded
   cudaGraphExec_t exec;
 };
 
@@ -39,6 +40,8 @@ struct omp_handle_s {
   float* y_stage = nullptr;
   float* x_stage = nullptr;
   int* s_stage = nullptr;
+  float* margin_buf = nullptr;                // Bmax x Smax per-step margins (when requested)
+  unsigned long long* cand2_buf = nullptr;    // FP32 path: runner-up keys (when requested)
   // profiling: events[(kind * Smax + k) * 2 + {0: start, 1: end}], kind 0 = correlate, 1 = update
   bool prof_on = false;
   int prof_last_S = 0;
@@ -106,11 +109,28 @@ omp_status check_launch() {
   return e == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
 }
 
-void enqueue_correlate(omp_handle_s* h, int k, int B, cudaStream_t s) {
-  if (h->ws.prec == OMP_PREC_FP32)
-    launch_corr_simt(h->ws, k, B, s);
+void enqueue_correlate(omp_handle_s* h, const Ws& ws, int k, int B, cudaStream_t s) {
+  if (ws.prec == OMP_PREC_FP32)
+    launch_corr_simt(ws, k, B, s);
   else
-    launch_corr_tc(h->ws, h->tc, k, B, s);
+    launch_corr_tc(ws, h->tc, k, B, s);
+}
+
+// The workspace view a solve runs with: the handle's own, or -- when the caller asks for each
+// step's top-two margin -- one whose kernels record it: the FP32 correlation also merges the
+// runner-up's key, and the quantised paths run without the score bound (every candidate
+// rescored in FP32, no pruning), which picks the same atoms (the exactness tests compare the two).
+Ws solve_ws(const omp_handle_s* h, bool stats) {
+  Ws w = h->ws;
+  if (stats) {
+    w.margin = h->margin_buf;
+    w.cand2 = w.prec == OMP_PREC_FP32 ? h->cand2_buf : nullptr;
+    w.rescore_eps = 0.f;
+    w.tau = nullptr;
+    w.tau_pos = nullptr;
+    w.ea = nullptr;
+  }
+  return w;
 }
 
 void prof_mark(omp_handle_s* h, bool prof, int kind, int k, int end, cudaStream_t s) {
@@ -119,13 +139,12 @@ void prof_mark(omp_handle_s* h, bool prof, int kind, int k, int end, cudaStream_
                            cudaEventRecordExternal);
 }
 
-void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStream_t s) {
-  const Ws& ws = h->ws;
+void enqueue_solve(omp_handle_s* h, const Ws& ws, int B, int S, float eps, bool prof, cudaStream_t s) {
   launch_init(ws, h->args_dev, B, s);
   launch_compact(ws, 0, B, S, false, s);
   for (int k = 0; k < S; ++k) {
     prof_mark(h, prof, 0, k, 0, s);
-    enqueue_correlate(h, k, B, s);
+    enqueue_correlate(h, ws, k, B, s);
     prof_mark(h, prof, 0, k, 1, s);
     prof_mark(h, prof, 1, k, 0, s);
     launch_update(ws, k, B, S, eps, h->d.eps_relative, s);
@@ -139,8 +158,7 @@ void enqueue_solve(omp_handle_s* h, int B, int S, float eps, bool prof, cudaStre
 // node): the body (correlate, update, compact, advance) reads the iteration from the counter
 // that the init kernel zeroes, and the advance kernel ends the loop after S iterations or as
 // soon as no signal is live, so a batch that converges early launches no further kernels.
-bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* out) {
-  const Ws& ws = h->ws;
+bool capture_while_solve(omp_handle_s* h, const Ws& ws, int B, int S, float eps, cudaGraph_t* out) {
   cudaStream_t s = h->cap_stream;
   *out = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
@@ -169,7 +187,7 @@ bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* 
     ok = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0,
                                        cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
-    enqueue_correlate(h, -1, B, h->body_stream);
+    enqueue_correlate(h, ws, -1, B, h->body_stream);
     launch_update(ws, -1, B, S, eps, h->d.eps_relative, h->body_stream);
     launch_compact(ws, -1, B, S, true, h->body_stream);
     launch_advance(ws, S, cond, h->body_stream);
@@ -192,11 +210,12 @@ bool capture_while_solve(omp_handle_s* h, int B, int S, float eps, cudaGraph_t* 
 void enqueue_topk(omp_handle_s* h, const float* R, int B, int topk, cudaStream_t s) {
   launch_load_rows(h->ws, R, B, s);
   launch_compact(h->ws, 0, B, 1, false, s);
-  enqueue_correlate(h, 0, B, s);
+  enqueue_correlate(h, h->ws, 0, B, s);
   launch_topk_out(h->ws, h->args_dev, B, topk, s);
 }
 
 omp_status prepare(omp_handle_s* h, const float* A, cudaStream_t s) {
+  if (h->ws.ea && cudaMemsetAsync(h->ws.ea, 0, sizeof(float), s) != cudaSuccess) return OMP_ERR_CUDA;
   launch_prep(h->ws, A, s);
   launch_gram_simt(h->ws, s);
   const omp_status st = check_launch();
@@ -204,16 +223,18 @@ omp_status prepare(omp_handle_s* h, const float* A, cudaStream_t s) {
   return st;
 }
 
-omp_status run_solve(omp_handle_s* h, int B, int S, float eps, cudaStream_t stream) {
+omp_status run_solve(omp_handle_s* h, int B, int S, float eps, bool stats, cudaStream_t stream) {
   const bool prof = h->prof_on;
   h->prof_last_S = S;
   h->prof_last_valid = prof;
+  const Ws ws = solve_ws(h, stats);
   if (!h->d.use_graph) {
-    enqueue_solve(h, B, S, eps, prof, stream);
+    enqueue_solve(h, ws, B, S, eps, prof, stream);
     return check_launch();
   }
   for (auto& g : h->graphs)
-    if (g.prof == static_cast<int>(prof) && g.B == B && g.S == S && g.eps == eps)
+    if (g.prof == static_cast<int>(prof) && g.stats == static_cast<int>(stats) && g.B == B &&
+        g.S == S && g.eps == eps)
       return cudaGraphLaunch(g.exec, stream) == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
   // capture on the handle's own stream (capture only records; the replay below runs in the
   // caller's stream order)
@@ -227,15 +248,15 @@ omp_status run_solve(omp_handle_s* h, int B, int S, float eps, cudaStream_t stre
   if (prof) {
     ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      enqueue_solve(h, B, S, eps, prof, h->cap_stream);
+      enqueue_solve(h, ws, B, S, eps, prof, h->cap_stream);
       ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
     }
   } else if (h->d.use_graph == 2) {
-    ok = capture_while_solve(h, B, S, eps, &graph);
+    ok = capture_while_solve(h, ws, B, S, eps, &graph);
   } else {
     ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      enqueue_solve(h, B, S, eps, false, h->cap_stream);
+      enqueue_solve(h, ws, B, S, eps, false, h->cap_stream);
       ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && graph != nullptr;
     }
   }
@@ -245,7 +266,7 @@ omp_status run_solve(omp_handle_s* h, int B, int S, float eps, cudaStream_t stre
     cudaGetLastError();
     return OMP_ERR_CUDA;
   }
-  h->graphs.push_back(GraphEntry{B, S, eps, static_cast<int>(prof), exec});
+  h->graphs.push_back(GraphEntry{B, S, eps, static_cast<int>(prof), static_cast<int>(stats), exec});
   return cudaGraphLaunch(exec, stream) == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
 }
 
@@ -324,7 +345,8 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   if (d.M < 1 || d.M > 8192 || d.N < 2 || d.N > 65536 || d.max_batch < 1 ||
       d.max_batch > (1 << 24) || d.max_iters < 1 || d.max_iters > 256 || d.max_iters > d.M ||
       d.max_iters > d.N || d.precision < 0 || d.precision > 2 || d.rescore_topk < 0 ||
-      d.rescore_topk > kMaxTopk || d.use_graph < 0 || d.use_graph > 2)
+      d.rescore_topk > kMaxTopk || d.use_graph < 0 || d.use_graph > 2 || d.gather24 < 0 ||
+      d.gather24 > 1)
     return OMP_ERR_INVALID_ARGUMENT;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || d.device < 0 || d.device >= ndev) {
@@ -356,6 +378,11 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   // (test hook: OMP_RESCORE_ALWAYS=1 turns the score bound, and all that uses it, off)
   const char* always = std::getenv("OMP_RESCORE_ALWAYS");
   ws.rescore_eps = always && std::atoi(always) == 1 ? 0.f : omp_score_error_bound(ws.prec, ws.Mp);
+  {
+    const double m = static_cast<double>(ws.Mp);
+    ws.gam_tc = static_cast<float>(m * std::ldexp(1.0, -22) / (1.0 - m * std::ldexp(1.0, -22)));
+    ws.gam_32 = static_cast<float>(m * std::ldexp(1.0, -24) / (1.0 - m * std::ldexp(1.0, -24)));
+  }
   // padded to 4 entries so each signal's FP32 factor starts on a 16-byte boundary
   ws.Fstride = (static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2 + 3) / 4 * 4;
   ws.upd_w = update_default_warps(ws.Mp);
@@ -365,6 +392,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   const size_t qbytes = d.precision == OMP_PREC_BF16 ? 2 : 1;
   bool ok = true;
   ok = ok && dalloc(h, &ws.A32, N * Mp);
+  if (d.gather24) ok = ok && dalloc(h, &ws.A24h, N * Mp) && dalloc(h, &ws.A24l, N * Mp);
   if (d.precision == OMP_PREC_BF16) ok = ok && dalloc(h, &ws.A16, N * Mp);
   if (d.precision == OMP_PREC_FP8_E4M3) ok = ok && dalloc(h, &ws.A8, N * Mp) && dalloc(h, &ws.sa, N);
   const size_t Npad = (N + 255) / 256 * 256;
@@ -381,8 +409,8 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
     ok = ok && dalloc(h, &ws.cand_s, Bp * ws.pieces * kMaxTopk) &&
          dalloc(h, &ws.cand_i, Bp * ws.pieces * kMaxTopk);
   }
-  if (ws.prec == OMP_PREC_BF16 && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
-    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp);
+  if (ws.prec != OMP_PREC_FP32 && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
+    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) && dalloc(h, &ws.ea, 1);
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
@@ -392,7 +420,9 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ok = ok && dalloc(h, &ws.ynorm, Bm) && dalloc(h, &ws.rnorm, Bm) && dalloc(h, &ws.niter, Bm) &&
        dalloc(h, &ws.stop, Bm) && dalloc(h, &ws.err, 1) && dalloc(h, &h->args_dev, 1);
   ok = ok && dalloc(h, &h->y_stage, Bm * static_cast<size_t>(ws.M)) &&
-       dalloc(h, &h->x_stage, Bm * Sm) && dalloc(h, &h->s_stage, Bm * Sm);
+       dalloc(h, &h->x_stage, Bm * Sm) && dalloc(h, &h->s_stage, Bm * Sm) &&
+       dalloc(h, &h->margin_buf, Bm * Sm);
+  if (d.precision == OMP_PREC_FP32) ok = ok && dalloc(h, &h->cand2_buf, Bm);
   if (!ok) {
     release(h);
     delete h;
@@ -401,6 +431,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   bool cuda_ok = cudaMemset(ws.err, 0, sizeof(unsigned)) == cudaSuccess &&
                  (!ws.escale || cudaMemset(ws.escale, 0, Npad * sizeof(float)) == cudaSuccess) &&
                  cudaMemset(ws.cand1, 0, Bm * sizeof(unsigned long long)) == cudaSuccess &&
+                 (!h->cand2_buf || cudaMemset(h->cand2_buf, 0, Bm * sizeof(unsigned long long)) == cudaSuccess) &&
                  (!ws.tau || cudaMemset(ws.tau, 0xff, Bm * sizeof(TauRec)) == cudaSuccess) &&
                  (!ws.tau_pos || cudaMemset(ws.tau_pos, 0, Bp * sizeof(float)) == cudaSuccess) &&
                  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
@@ -437,7 +468,8 @@ omp_status omp_prepare_dictionary(omp_handle h, const float* A, void* stream) {
 
 omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
                               float eps, float* X_out, int32_t* support_out, int32_t* n_iter_out,
-                              float* resid_norm_out, int32_t* stop_out, void* stream) {
+                              float* resid_norm_out, float* margin_out, int32_t* stop_out,
+                              void* stream) {
   omp_status st = validate_solve(h, A, Y, B, S, eps, X_out, support_out);
   if (st != OMP_OK) return st;
   DeviceGuard guard(h->dev);
@@ -453,10 +485,11 @@ omp_status omp_solve_batch_ex(omp_handle h, const float* A, const float* Y, int6
   a.n_iter = n_iter_out;
   a.resid = resid_norm_out;
   a.stop = stop_out;
+  a.margin = margin_out;
   launch_set_args(h->args_dev, a, s);
   st = check_launch();
   if (st != OMP_OK) return st;
-  return run_solve(h, static_cast<int>(B), S, eps, s);
+  return run_solve(h, static_cast<int>(B), S, eps, margin_out != nullptr, s);
 }
 
 omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
@@ -478,7 +511,7 @@ omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, i
   launch_set_args(h->args_dev, a, s);
   st = check_launch();
   if (st != OMP_OK) return st;
-  return run_solve(h, static_cast<int>(B), S, eps, s);
+  return run_solve(h, static_cast<int>(B), S, eps, false, s);
 }
 
 omp_status omp_solve_batch_gram(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
@@ -578,7 +611,7 @@ omp_status solve_candidates(omp_handle h, const float* A, const float* Y, int64_
   // signals that failed the residual-drop check continue in the dense loop
   launch_compact(ws, 0, b, S, false, s);
   for (int k = 0; k < S; ++k) {
-    enqueue_correlate(h, k, b, s);
+    enqueue_correlate(h, ws, k, b, s);
     launch_update(ws, k, b, S, eps, h->d.eps_relative, s);
     if (k + 1 < S) launch_compact(ws, k + 1, b, S, true, s);
   }
@@ -633,9 +666,9 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       if (!update_slots(h->ws.Mp, w)) continue;
       h->ws.upd_w = w;
       launch_set_args(h->args_dev, a, s);
-      enqueue_solve(h, static_cast<int>(B), S, eps, false, s);  // warm-up
+      enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);  // warm-up
       cudaEventRecord(e0, s);
-      for (int r = 0; r < repeats; ++r) enqueue_solve(h, static_cast<int>(B), S, eps, false, s);
+      for (int r = 0; r < repeats; ++r) enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);
       cudaEventRecord(e1, s);
       float ms = 0.f;
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -689,7 +722,7 @@ omp_status omp_loop_passes(omp_handle h, int32_t* passes_out, void* stream) {
 omp_status omp_solve_batch(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S,
                            float eps, float* X_out, int32_t* support_out, void* stream) {
   return omp_solve_batch_ex(h, A, Y, B, S, eps, X_out, support_out, nullptr, nullptr, nullptr,
-                            stream);
+                            nullptr, stream);
 }
 
 omp_status omp_solve_batch_host(omp_handle h, const float* A, const float* Y_host, int64_t B,
@@ -703,7 +736,7 @@ omp_status omp_solve_batch_host(omp_handle h, const float* A, const float* Y_hos
   if (cudaMemcpyAsync(h->y_stage, Y_host, ybytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return OMP_ERR_CUDA;
   omp_status st = omp_solve_batch_ex(h, A, h->y_stage, B, S, eps, h->x_stage, h->s_stage, nullptr,
-                                     nullptr, nullptr, stream);
+                                     nullptr, nullptr, nullptr, stream);
   if (st != OMP_OK) return st;
   const size_t obytes = static_cast<size_t>(B) * S * sizeof(float);
   if (cudaMemcpyAsync(X_host, h->x_stage, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, 
     ws.flag[b] = alive ? 1 : 0;
     ws.fb[b] = -1;
     ws.live[1][b] = b;
-    if (ws.tau) ws.tau[b] = TauRec{0.f, -1};
+    if (ws.tau) ws.tau[b] = TauRec{0.f, 0.f, -1, 0};
     if (!finite) atomicOr(ws.err, OMP_DEVERR_NONFINITE);
     if (b == 0) ws.cnt[0] = B;
   }
@@ -146,15 +146,27 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (r < 0) continue;
     const int dest = before + r;
     const int id = in[p0 + i];
+    // the threshold the update kernel of step j - 1 wrote for this signal, for the correlation
+    // (FP8: in the units of the scores, which leave out the row's scale)
+    float tau = 0.f;
+    if (ws.tau_pos && j > 0) {
+      const TauRec t = ws.tau[id];
+      tau = t.step == j && t.tau > 0.f ? t.tau : 0.f;
+    }
+    const bool fp8_tau = tau > 0.f && ws.prec == OMP_PREC_FP8_E4M3;
     if (lane == 0) {
       out[dest] = id;
       ws.cand1[dest] = 0ull;
-      if (ws.tau_pos) {  // the update kernel of step j - 1 wrote this signal's threshold
-        const TauRec t = j > 0 ? ws.tau[id] : TauRec{0.f, -1};
-        ws.tau_pos[dest] = t.step == j && t.tau > 0.f ? t.tau : 0.f;
-      }
+      if (ws.cand2) ws.cand2[dest] = 0ull;
+      if (ws.tau_pos && !fp8_tau) ws.tau_pos[dest] = tau;
     }
-    if (rows_in_place) continue;
+    if (rows_in_place) {
+      if (lane == 0 && fp8_tau) {  // the row's scale was written with it by the update kernel
+        const float sr = ws.sr[j & 1][dest];
+        ws.tau_pos[dest] = sr > 0.f ? tau / sr : 0.f;
+      }
+      continue;
+    }
     const float4* src = reinterpret_cast<const float4*>(ws.R32 + static_cast<size_t>(id) * ws.Mp);
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
@@ -190,7 +202,11 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
       }
       amax = warp_max(amax);
       const float inv = amax > 0.f ? 448.f / amax : 0.f;
-      if (lane == 0) ws.sr[j & 1][dest] = amax > 0.f ? amax / 448.f : 0.f;
+      const float sr = amax > 0.f ? amax / 448.f : 0.f;
+      if (lane == 0) {
+        ws.sr[j & 1][dest] = sr;
+        if (fp8_tau) ws.tau_pos[dest] = sr > 0.f ? tau / sr : 0.f;
+      }
       uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws.Rq[j & 1]) +
                                                   static_cast<size_t>(dest) * ws.Mp);
       for (int m0 = 0; m0 < M4; m0 += 256) {
@@ -262,6 +278,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(Ws ws, const CallArgs* ar
     const float* dg = ws.drop + static_cast<size_t>(b) * ws.Smax;
     float* dd = args->drop + static_cast<size_t>(b) * S;
     for (int i = lane; i < S; i += 32) dd[i] = i < n ? dg[i] : 0.f;
+  }
+  if (args->margin && ws.margin) {
+    const float* mg = ws.margin + static_cast<size_t>(b) * ws.Smax;
+    float* md = args->margin + static_cast<size_t>(b) * S;
+    for (int i = lane; i < S; i += 32) md[i] = i < n ? mg[i] : -1.f;
   }
   if (lane == 0) {
     if (args->n_iter) args->n_iter[b] = n;

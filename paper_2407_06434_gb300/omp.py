@@ -38,7 +38,7 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
            "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
            "omp_loop_passes", "omp_read_bandwidth_probe", "omp_solve_batch_gram",
-           "omp_score_error_bound"]
+           "omp_score_error_bound", "omp_proposal_save", "omp_proposal_load"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -46,7 +46,8 @@ class omp_desc(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("max_batch", ctypes.c_int64),
                 ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rescore_topk", ctypes.c_int32), ("eps_relative", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("gather24", ctypes.c_int32)]
 
 
 class omp_proposal_desc(ctypes.Structure):
@@ -83,7 +84,7 @@ def load(path: Optional[str] = None):
         "omp_destroy": (_I32, [_P]),
         "omp_prepare_dictionary": (_I32, [_P, _P, _P]),
         "omp_solve_batch": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P]),
-        "omp_solve_batch_ex": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
+        "omp_solve_batch_ex": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P, _P]),
         "omp_solve_batch_host": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _P, _P]),
         "omp_correlate_topk": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P]),
         "omp_get_error": (_I32, [_P, ctypes.POINTER(_I32), _P]),
@@ -108,6 +109,8 @@ def load(path: Optional[str] = None):
         "omp_proposal_set_thresholds": (_I32, [_P, _P, _I32]),
         "omp_proposal_get_thresholds": (_I32, [_P, _P, _I32]),
         "omp_proposal_calibrate": (_I32, [_P, _P, _I64, _I32, _F32, _P]),
+        "omp_proposal_save": (_I32, [_P, ctypes.c_char_p]),
+        "omp_proposal_load": (_I32, [_P, ctypes.c_char_p]),
         "omp_topk_rows": (_I32, [_P, _I64, _I64, _I32, _P, _P]),
         "omp_proposal_baseline_candidates": (_I32, [_P, _P, _P, _I64, _P, _P]),
         "omp_solve_batch_candidates": (_I32, [_P, _P, _P, _I64, _I32, _F32, _P, _I32, _P, _P, _P, _P,
@@ -178,7 +181,7 @@ class Handle:
 
 def omp_create(M: int, N: int, max_batch: int = 4096, max_iters: int = 64,
                precision: str = "bf16", rescore_topk: int = 8, eps_relative: bool = True,
-               use_graph: int = 1, device: int = 0) -> Handle:
+               use_graph: int = 1, device: int = 0, gather24: bool = False) -> Handle:
     lib = load()
     d = omp_desc()
     lib.omp_desc_default(ctypes.byref(d), M, N)
@@ -186,6 +189,7 @@ def omp_create(M: int, N: int, max_batch: int = 4096, max_iters: int = 64,
     d.precision = PRECISIONS[precision]
     d.rescore_topk, d.eps_relative = rescore_topk, int(eps_relative)
     d.use_graph, d.device = int(use_graph), device
+    d.gather24 = int(gather24)
     h = ctypes.c_void_p()
     _check(lib.omp_create(ctypes.byref(d), ctypes.byref(h)), "omp_create")
     return Handle(h, d)
@@ -211,12 +215,15 @@ def omp_solve_batch(h: Handle, A, Y, S: int, eps: float, X_out, support_out, str
 
 
 def omp_solve_batch_ex(h: Handle, A, Y, S: int, eps: float, X_out, support_out, n_iter_out=None,
-                       resid_norm_out=None, stop_out=None, stream=None):
+                       resid_norm_out=None, stop_out=None, stream=None, margin_out=None):
+    """Outputs as omp_solve_batch plus the optional diagnostics; margin_out (B, S) float32 asks
+    for each step's top-two score margin (see include/omp_gb300.h)."""
     _check_A(A, h.M, h.N)
     B = Y.shape[0]
     _check(load().omp_solve_batch_ex(h.ptr, _ptr(A), _ptr(Y), B, S, eps, _ptr(X_out),
                                      _ptr(support_out), _ptr(n_iter_out), _ptr(resid_norm_out),
-                                     _ptr(stop_out), _stream(stream)), "omp_solve_batch_ex")
+                                     _ptr(margin_out), _ptr(stop_out), _stream(stream)),
+           "omp_solve_batch_ex")
 
 
 def omp_solve_batch_gram(h: Handle, A, Y, S: int, eps: float, X_out, support_out, n_iter_out=None,
@@ -441,6 +448,14 @@ class Proposal:
                "omp_proposal_get_thresholds")
         return t
 
+    def save(self, path: str):
+        """Write the weights and thresholds to `path` (omp_proposal_save)."""
+        _check(load().omp_proposal_save(self.ptr, os.fsencode(path)), "omp_proposal_save")
+
+    def load(self, path: str):
+        """Read weights and thresholds saved by save() for the same N and hidden width."""
+        _check(load().omp_proposal_load(self.ptr, os.fsencode(path)), "omp_proposal_load")
+
     def calibrate(self, drops, quantile=1e-3, stream=None):
         _check(load().omp_proposal_calibrate(self.ptr, _ptr(drops), drops.shape[0], drops.shape[1],
                                              quantile, _stream(stream)), "omp_proposal_calibrate")
@@ -484,19 +499,24 @@ class OmpSolver:
         omp_solve_batch_gram(self.h, A, Y, S, eps, X, sup, n_iter, resid, stop, stream)
         return (X, sup, n_iter, resid, stop) if diagnostics else (X, sup)
 
-    def solve(self, A, Y, S, eps=0.0, stream=None, diagnostics=False):
+    def solve(self, A, Y, S, eps=0.0, stream=None, diagnostics=False, margins=False):
+        """(X, support), or with diagnostics (X, support, n_iter, resid_norm, stop), plus the
+        (B, S) per-step margins last when margins=True."""
         import torch
         B = Y.shape[0]
         X = torch.empty((B, S), dtype=torch.float32, device=Y.device)
         sup = torch.empty((B, S), dtype=torch.int32, device=Y.device)
-        if not diagnostics:
+        if not diagnostics and not margins:
             omp_solve_batch(self.h, A, Y, S, eps, X, sup, stream)
             return X, sup
         n_iter = torch.empty(B, dtype=torch.int32, device=Y.device)
         resid = torch.empty(B, dtype=torch.float32, device=Y.device)
         stop = torch.empty(B, dtype=torch.int32, device=Y.device)
-        omp_solve_batch_ex(self.h, A, Y, S, eps, X, sup, n_iter, resid, stop, stream)
-        return X, sup, n_iter, resid, stop
+        margin = torch.empty((B, S), dtype=torch.float32, device=Y.device) if margins else None
+        omp_solve_batch_ex(self.h, A, Y, S, eps, X, sup, n_iter, resid, stop, stream,
+                           margin_out=margin)
+        out = (X, sup, n_iter, resid, stop) if diagnostics else (X, sup)
+        return out + (margin,) if margins else out
 
     def close(self):
         omp_destroy(self.h)

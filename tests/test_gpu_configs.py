@@ -44,12 +44,12 @@ def check_rows(B, n=N_CHECK, seed=0):
     return np.sort(np.random.default_rng(seed).choice(B, n, replace=False))
 
 
-def run_config(name, prec, n_check=N_CHECK, **overrides):
+def run_config(name, prec, n_check=N_CHECK, solver_kw=None, **overrides):
     from paper_2407_06434_gb300 import omp
     w = gen.get_config(name, **overrides)
     A = gen.dictionary(w)
     Y, sp, sup, coef = gen.signals(w, A)
-    s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
+    s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec, **(solver_kw or {}))
     Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
     X, S_, n_iter, resid, stop = s.solve(Ad, torch.from_numpy(Y).cuda(), w.S, w.eps, diagnostics=True)
     torch.cuda.synchronize()
@@ -79,6 +79,16 @@ def test_coherent_4096x32768_fp8():
     w, st, n_iter, S_, sup = run_config("coherent_4096x32768_s64_b16384", "fp8")
     assert st["tie_diverged"] <= 0.02 * st["signals"], st
     assert np.all(n_iter == w.S)
+
+
+def test_coherent_4096x32768_fp8_gather24():
+    """The same workload with the update's atom-row gather reading the 24-bit copy of A (3 bytes
+    per element): the same parity bar against the FP64 oracle."""
+    w, st, n_iter, S_, sup = run_config("coherent_4096x32768_s64_b16384", "fp8",
+                                        solver_kw=dict(gather24=True))
+    assert st["tie_diverged"] <= 0.02 * st["signals"], st
+    assert np.all(n_iter == w.S)
+    assert st["max_coef_rel"] <= 1e-4
 
 
 def test_learned_workload_dense_1024x8192_s48():

@@ -114,6 +114,49 @@ def test_inference_logits_and_candidates(lib):
     h.close()
 
 
+def test_proposal_save_and_load(lib, tmp_path):
+    """omp_proposal_save / omp_proposal_load through the C ABI: a second proposal loaded from the
+    file has bit-identical weights, beta and thresholds and proposes the same candidates; a file
+    with one byte changed, a truncated file and a proposal of another width are refused."""
+    omp = lib
+    w, A, Y, sup = _small_problem(B=100, seed=3)
+    h, p, params = _proposal(omp, w, hidden=64, topk=24, train_batch=64, max_batch=100, pw=3.0)
+    tau = np.linspace(0.01, 0.2, w.S).astype(np.float32)
+    p.set_thresholds(tau)
+    path = str(tmp_path / "proposal.bin")
+    p.save(path)
+    q = omp.Proposal(h.h, hidden=64, topk=24, max_batch=100, train_batch=64, pos_weight=3.0)
+    q.load(path)
+    shapes = [(64, w.N), (64,), (w.N, 64), (w.N,), (1,)]
+    got = [torch.empty(sh, device="cuda") for sh in shapes]
+    q.get_weights(*got)
+    for g, want in zip(got, params):
+        assert np.array_equal(g.cpu().numpy().reshape(-1).view(np.uint32),
+                              np.asarray(want, dtype=np.float32).reshape(-1).view(np.uint32))
+    assert np.array_equal(q.get_thresholds(w.S), tau)
+    Ad, Yd = dev_dict(A), cuda(Y)
+    c1 = torch.empty((100, 24), dtype=torch.int32, device="cuda")
+    c2 = torch.empty((100, 24), dtype=torch.int32, device="cuda")
+    p.infer(Ad, Yd, c1)
+    q.infer(Ad, Yd, c2)
+    assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
+    raw = bytearray(open(path, "rb").read())
+    bad = tmp_path / "bad.bin"
+    raw2 = bytearray(raw)
+    raw2[len(raw2) // 2] ^= 0x40
+    bad.write_bytes(bytes(raw2))
+    for data in (bytes(raw2), bytes(raw[:-9])):
+        bad.write_bytes(data)
+        with pytest.raises(omp.OmpError):
+            q.load(str(bad))
+    other = omp.Proposal(h.h, hidden=128, topk=24, max_batch=100, train_batch=64, pos_weight=3.0)
+    with pytest.raises(omp.OmpError):
+        other.load(path)
+    for x in (other, q, p):
+        x.close()
+    h.close()
+
+
 def _solve_candidates(omp, A, Y, S, cand, tau, eps=0.0):
     M, N = A.shape
     B = Y.shape[0]

@@ -34,12 +34,14 @@ def dev_dict(A):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float32).T)).cuda().t()
 
 
-def solve(prec, A, Y, S, eps=0.0, eps_relative=True, use_graph=True, max_batch=None, topk=8):
+def solve(prec, A, Y, S, eps=0.0, eps_relative=True, use_graph=True, max_batch=None, topk=8,
+          gather24=False):
     from paper_2407_06434_gb300 import omp
     M, N = A.shape
     B = Y.shape[0]
     s = omp.OmpSolver(M, N, max_batch=max_batch or B, max_iters=S, precision=prec,
-                      eps_relative=eps_relative, use_graph=use_graph, rescore_topk=topk)
+                      eps_relative=eps_relative, use_graph=use_graph, rescore_topk=topk,
+                      gather24=gather24)
     Ad = dev_dict(A)
     Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).cuda()
     X, sup, n_iter, resid, stop = s.solve(Ad, Yd, S, eps, diagnostics=True)
@@ -91,6 +93,45 @@ def test_ragged_tiles(prec):
     r = solve(prec, A, Y, w.S)
     st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"])
     assert st["tie_diverged"] <= 3, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gather24_signal_level_steps(prec):
+    """The 24-bit gather option (q = A_S F[:,k] from A rounded to a 15-bit mantissa, 3 bytes per
+    element) against the FP64 oracle where every step picks at signal level: ragged tiles
+    (M = 200, N = 1000, B = 300), S = each signal's planted sparsity (5..24) with coefficients of
+    magnitude in [0.5, 1] and noise 1e-3, then an eps-stopped uneven batch (noise 1e-6, signals
+    retire near their sparsity). Same parity bar as the FP32 rows; results move by rounding only
+    (coefficients within 2e-5 of the FP32-gather solve). Past the noise floor the option moves
+    picks at margins up to ~2e-3 (the rounding of q, 2^-16 of ||y||, is then no longer small
+    next to the scores), so it is for solves that stop at signal level."""
+    w = gen.get_config("gaussian_64x256_s8_b16", M=200, N=1000, B=300, S=24, s_min=5, s_max=24,
+                       sigma=1e-3, col_scale=1.0, coef_kind="signed_uniform")
+    A = gen.dictionary(w, seed=3)
+    Y, sp, sup, coef = gen.signals(w, A, seed=3)
+    rows = [np.flatnonzero(sp == s_) for s_ in np.unique(sp)]
+    n_div = n_same = 0
+    for rr in rows:
+        S = int(sp[rr[0]])
+        ref = oracle.omp_batch(A, Y[rr], S)
+        r = solve(prec, A, Y[rr], S, gather24=True)
+        st = parity.compare(A, Y[rr], ref, r["sup"], r["X"], r["n_iter"], r["resid"])
+        n_div += st["tie_diverged"]
+        r32 = solve(prec, A, Y[rr], S)
+        same = np.all(r["sup"] == r32["sup"], axis=1)
+        n_same += int(same.sum())
+        d = np.linalg.norm(r["X"][same] - r32["X"][same], axis=1) / np.linalg.norm(r32["X"][same], axis=1)
+        assert d.size == 0 or d.max() <= 2e-5, d.max()
+    assert n_div <= 2 and n_same >= w.B - 2, (n_div, n_same)
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=2048, B=200, S=48, s_min=4, s_max=40,
+                       sigma=1e-6, col_scale=1.0)
+    A = gen.dictionary(w, seed=4)
+    Y, *_ = gen.signals(w, A, seed=4)
+    ref = oracle.omp_batch(A, Y, w.S, 1e-3)
+    r = solve(prec, A, Y, w.S, eps=1e-3, gather24=True)
+    st = parity.compare(A, Y, ref, r["sup"], r["X"], r["n_iter"], r["resid"], eps=1e-3)
+    assert np.mean(r["stop"] == oracle.STOP_EPS) > 0.9
+    assert st["tie_diverged"] <= 2, st
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -502,3 +543,44 @@ def test_handles_with_different_layouts_coexist():
     assert np.array_equal(G0[1].cpu().numpy(), G1[1].cpu().numpy())
     for s in small + [small_gram, big]:
         s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_margins_against_the_oracle(prec):
+    """margin_out of omp_solve_batch_ex: the top-two score margin (s1 - s2) / s1 of every step,
+    against the FP64 oracle's on a noisy ragged batch (several atom and signal tiles). Asking
+    for margins changes no result (supports and coefficients bit-identical to the same solve
+    without them). FP32: equal to the oracle's within 5e-5 at every step of every signal whose
+    support is the oracle's. Quantised paths (margins over the FP32 scores of the rescored
+    candidates): never below the oracle's by more than 5e-5 (the runner-up can only be missed,
+    which raises the margin), and equal to it at most steps. -1 past each signal's last step."""
+    from paper_2407_06434_gb300 import omp
+    w = gen.get_config("gaussian_64x256_s8_b16", M=200, N=1000, B=300, S=24, s_min=5, s_max=24,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=3)
+    Y, *_ = gen.signals(w, A, seed=3)
+    ref = oracle.omp_batch(A, Y, w.S)
+    s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
+    Ad, Yd = dev_dict(A), torch.from_numpy(Y).cuda()
+    X0, S0 = s.solve(Ad, Yd, w.S)
+    X1, S1, n_iter, resid, stop, mg = s.solve(Ad, Yd, w.S, diagnostics=True, margins=True)
+    X2, S2 = s.solve(Ad, Yd, w.S)                    # the plain graph again after the stats one
+    torch.cuda.synchronize()
+    s.close()
+    for Xa, Sa in ((X1, S1), (X2, S2)):
+        assert np.array_equal(Sa.cpu().numpy(), S0.cpu().numpy())
+        assert np.array_equal(Xa.cpu().numpy().view(np.uint32), X0.cpu().numpy().view(np.uint32))
+    sup, mg, n_iter = S1.cpu().numpy(), mg.cpu().numpy(), n_iter.cpu().numpy()
+    for b in range(w.B):
+        assert np.all(mg[b, n_iter[b]:] == -1.0)
+    same = np.all(sup == ref.support, axis=1)
+    assert same.mean() > 0.95
+    steps = np.arange(w.S)[None, :] < n_iter[:, None]
+    sel = same[:, None] & steps
+    diff = mg[sel] - ref.margin[sel]
+    assert np.all(np.isfinite(diff))
+    if prec == "fp32":
+        assert np.max(np.abs(diff)) <= 5e-5, np.max(np.abs(diff))
+    else:
+        assert diff.min() >= -5e-5, diff.min()
+        assert np.mean(np.abs(diff) <= 5e-5) >= (0.8 if prec == "bf16" else 0.3)

@@ -633,7 +633,8 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     // The next step's quantised operand row, at this position: the compaction keeps it where
     // no signal before this one retired, and re-quantises from R32 otherwise. Same rounding as
     // the compaction's (BF16 round-to-nearest-even; E4M3 satfinite with the row's amax / 448).
-    // The squared norm of its rounding error feeds the next step's data-driven score bound.
+    // E4M3: the squared norm of its rounding error feeds the next step's data-driven score bound
+    // (BF16 keeps the worst case, already tight enough to prune, which costs nothing here).
     const int j = (k + 1) & 1;
     float e2 = 0.f;
     if (ws.prec == OMP_PREC_BF16) {
@@ -647,9 +648,6 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
           const __nv_bfloat162 h1 = __floats2bfloat162_rn(r[t].z, r[t].w);
           dq[2 * s] = h0;
           dq[2 * s + 1] = h1;
-          const float2 g0 = __bfloat1622float2(h0), g1 = __bfloat1622float2(h1);
-          const float d0 = g0.x - r[t].x, d1 = g0.y - r[t].y, d2 = g1.x - r[t].z, d3 = g1.y - r[t].w;
-          e2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
         }
       }
     } else {
@@ -685,7 +683,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         }
       }
     }
-    qe2 = warp_sum_f(e2);
+    if (ws.prec == OMP_PREC_FP8_E4M3) qe2 = warp_sum_f(e2);
   }
   if (lane == 0) pf[8 + wig] = rr;
   group_sync(W, grp);

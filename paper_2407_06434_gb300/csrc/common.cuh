@@ -62,6 +62,7 @@ struct Ws {
   int tc_grid;     // tensor-core correlation: persistent grid size
   int tc_tn;       // atom tiles of 256
   int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
+  int tc_stages;   // operand stages of the correlation's pipeline (2..4; autotuned)
   int upd_w;       // append/update kernel: warps per signal (1, 2, 4, 8; autotuned)
   int64_t Fstride; // Smax (Smax + 1) / 2 rounded up to a multiple of 4
   // dictionary

@@ -54,8 +54,8 @@ bool make_kmajor_map(CUtensorMap* m, const void* ptr, int prec, uint64_t rows, u
   return r == CUDA_SUCCESS;
 }
 
-cudaError_t set_smem_attr(const void* kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+cudaError_t set_smem_attr(const void* kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace tcg
@@ -250,7 +250,7 @@ struct EpiTop8 {
   }
 };
 
-template <int PREC>
+template <int PREC, int NST>
 __global__ void __launch_bounds__(THREADS, 1)
     corr_tc_kernel(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
                    const __grid_constant__ CUtensorMap tm_a, Ws ws, int k) {
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   epi.L = L;
   const int row_tiles = (L + BM - 1) / BM;
   const int ktiles = ws.Mp * (PREC == OMP_PREC_BF16 ? 2 : 1) / KB;
-  gemm_body<PREC>((k & 1) ? &tm_r1 : &tm_r0, &tm_a, row_tiles, ws.tc_tn, ktiles, ws.tc_cmin,
-                  ws.err, epi);
+  gemm_body<PREC, EpiTop8<PREC>, NST>((k & 1) ? &tm_r1 : &tm_r0, &tm_a, row_tiles, ws.tc_tn, ktiles,
+                                      ws.tc_cmin, ws.err, epi);
 }
 
 }  // namespace
@@ -277,6 +277,7 @@ int tc_pieces() { return kPieces; }
 
 void tc_fill_sched(Ws& ws, int sm_count) {
   ws.tc_grid = sm_count;
+  ws.tc_stages = STAGES;
   ws.tc_tn = (ws.N + BN - 1) / BN;
   // a tile of Tn units meets at most ceil(Tn / cmin) + 1 CTA ranges of >= cmin units
   constexpr int kMaxPieces = kPieces / EPI_PARTS;
@@ -295,8 +296,16 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
     delete p;
     return cudaErrorNotSupported;
   }
-  cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16>));
-  if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3>));
+  cudaError_t e = cudaSuccess;
+  auto attr = [&](const void* kern, int nst) {
+    if (e == cudaSuccess) e = set_smem_attr(kern, smem_bytes(nst));
+  };
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 4>), 4);
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 3>), 3);
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 2>), 2);
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 4>), 4);
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 3>), 3);
+  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 2>), 2);
   if (e != cudaSuccess) {
     delete p;
     return e;
@@ -307,12 +316,24 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
 
 void tc_destroy(TcPlan* plan) { delete plan; }
 
+template <int PREC>
+void launch_prec(const Ws& ws, const TcPlan* plan, int k, cudaStream_t s) {
+  // the persistent grid is the workspace's (the candidate slots are laid out for it)
+  const int grid = ws.tc_grid;
+  if (ws.tc_stages == 3)
+    corr_tc_kernel<PREC, 3><<<grid, THREADS, smem_bytes(3), s>>>(plan->r0, plan->r1, plan->a, ws, k);
+  else if (ws.tc_stages == 2)
+    corr_tc_kernel<PREC, 2><<<grid, THREADS, smem_bytes(2), s>>>(plan->r0, plan->r1, plan->a, ws, k);
+  else
+    corr_tc_kernel<PREC, 4><<<grid, THREADS, smem_bytes(4), s>>>(plan->r0, plan->r1, plan->a, ws, k);
+}
+
 void launch_corr_tc(const Ws& ws, const TcPlan* plan, int k, int B, cudaStream_t s) {
   (void)B;
   if (ws.prec == OMP_PREC_BF16)
-    corr_tc_kernel<OMP_PREC_BF16><<<plan->grid, THREADS, SMEM_BYTES, s>>>(plan->r0, plan->r1, plan->a, ws, k);
+    launch_prec<OMP_PREC_BF16>(ws, plan, k, s);
   else
-    corr_tc_kernel<OMP_PREC_FP8_E4M3><<<plan->grid, THREADS, SMEM_BYTES, s>>>(plan->r0, plan->r1, plan->a, ws, k);
+    launch_prec<OMP_PREC_FP8_E4M3>(ws, plan, k, s);
 }
 
 }  // namespace ompk

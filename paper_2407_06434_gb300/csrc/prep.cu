@@ -45,17 +45,12 @@ __global__ void __launch_bounds__(256) prep_kernel(Ws ws, const float* __restric
         l[m] = static_cast<uint8_t>(r >> 8);
       }
     }
-    // e2: squared norm of the quantisation error of the atom as the correlation sees it (the BF16
-    // value, or the E4M3 code times the atom's scale), for the data-driven score bound
+    // e2: squared norm of the quantisation error of the atom as the correlation sees it (the E4M3
+    // code times the atom's scale), for the data-driven score bound of the E4M3 path
     double e2 = 0.0;
     if (ws.prec == OMP_PREC_BF16) {
       __nv_bfloat16* a16 = ws.A16 + static_cast<size_t>(n) * ws.Mp;
-      for (int m = lane; m < ws.Mp; m += 32) {
-        const __nv_bfloat16 q = __float2bfloat16_rn(a32[m]);
-        a16[m] = q;
-        const double d = static_cast<double>(__bfloat162float(q)) - static_cast<double>(a32[m]);
-        e2 += d * d;
-      }
+      for (int m = lane; m < ws.Mp; m += 32) a16[m] = __float2bfloat16_rn(a32[m]);
     } else if (ws.prec == OMP_PREC_FP8_E4M3) {
       const float inv = amax > 0.f ? 448.f / amax : 0.f;
       const float sa = amax > 0.f ? amax / 448.f : 0.f;

@@ -409,8 +409,14 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
     ok = ok && dalloc(h, &ws.cand_s, Bp * ws.pieces * kMaxTopk) &&
          dalloc(h, &ws.cand_i, Bp * ws.pieces * kMaxTopk);
   }
-  if (ws.prec != OMP_PREC_FP32 && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
-    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) && dalloc(h, &ws.ea, 1);
+  // The pruning thresholds (and the data-driven bound they carry): on BF16 always; on E4M3,
+  // whose worst-case bound is too loose to prune, only where the one-warp update quantises the
+  // next row itself and so can measure its rounding error (padded lengths up to 1024).
+  const bool want_tau = ws.prec == OMP_PREC_BF16 ||
+                        (ws.prec == OMP_PREC_FP8_E4M3 && update_default_warps(ws.Mp) == 1);
+  if (want_tau && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
+    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) &&
+         (ws.prec != OMP_PREC_FP8_E4M3 || dalloc(h, &ws.ea, 1));
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
@@ -632,39 +638,50 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   char key[256];
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, h->dev) != cudaSuccess) return OMP_ERR_CUDA;
-  std::snprintf(key, sizeof(key), "%s M=%d N=%d prec=%d B=%lld S=%d", prop.name, h->ws.M, h->ws.N,
+  std::snprintf(key, sizeof(key), "%.64s M=%d N=%d prec=%d B=%lld S=%d", prop.name, h->ws.M, h->ws.N,
                 h->ws.prec, static_cast<long long>(B), S);
-  int best = 0;
-  if (cache) {  // a previous run's choice for the same key
+  const bool tc = h->ws.prec != OMP_PREC_FP32;
+  // a launch shape: update warps per signal, correlation stages and persistent CTAs
+  struct Shape {
+    int w, stages, grid;
+  };
+  auto valid = [&](const Shape& c) {
+    return update_slots(h->ws.Mp, c.w) != 0 &&
+           (!tc || (c.stages >= 2 && c.stages <= 4 && c.grid >= 1 && c.grid <= h->sm_count));
+  };
+  const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid};
+  Shape best{0, saved.stages, saved.grid};
+  if (cache) {  // a previous run's choice for the same key: "key|w" or "key|w,stages,grid"
     if (FILE* f = std::fopen(cache, "r")) {
       char line[512];
       while (std::fgets(line, sizeof(line), f)) {
-        int w = 0;
         char* bar = std::strrchr(line, '|');
-        if (bar && std::strncmp(line, key, std::strlen(key)) == 0 && line[std::strlen(key)] == '|' &&
-            std::sscanf(bar + 1, "%d", &w) == 1 && update_slots(h->ws.Mp, w))
-          best = w;
+        Shape c = saved;
+        const int n = bar ? std::sscanf(bar + 1, "%d,%d,%d", &c.w, &c.stages, &c.grid) : 0;
+        if (std::strncmp(line, key, std::strlen(key)) == 0 && line[std::strlen(key)] == '|' &&
+            (n == 1 || n == 3) && valid(c))
+          best = c;
       }
       std::fclose(f);
     }
   }
-  if (!best) {
+  if (!best.w) {
     omp_status st = OMP_OK;
     if (A != h->prepared_A) st = prepare(h, A, s);
     if (st != OMP_OK) return st;
-    float* X = h->x_stage;
-    int* sup = h->s_stage;
     CallArgs a{};
     a.Y = Y;
-    a.X = X;
-    a.support = sup;
+    a.X = h->x_stage;
+    a.support = h->s_stage;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OMP_ERR_CUDA;
     float best_ms = 0.f;
-    const int saved = h->ws.upd_w;
-    for (int w = 1; w <= 8; w <<= 1) {
-      if (!update_slots(h->ws.Mp, w)) continue;
-      h->ws.upd_w = w;
+    bool failed = false;
+    auto trial = [&](const Shape& c) {
+      if (failed || !valid(c)) return;
+      h->ws.upd_w = c.w;
+      h->ws.tc_stages = c.stages;
+      h->ws.tc_grid = c.grid;
       launch_set_args(h->args_dev, a, s);
       enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);  // warm-up
       cudaEventRecord(e0, s);
@@ -672,32 +689,61 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       cudaEventRecord(e1, s);
       float ms = 0.f;
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        h->ws.upd_w = saved;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return OMP_ERR_CUDA;
+        failed = true;
+        return;
       }
-      if (!best || ms < best_ms) {
-        best = w;
+      if (!best.w || ms < best_ms) {
+        best = c;
         best_ms = ms;
       }
+    };
+    // the update's warps per signal first (with the default correlation), then the correlation's
+    // pipeline depth and grid with the best of those
+    for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid});
+    if (tc && !failed) {
+      const Shape b0 = best;
+      for (int st = 4; st >= 2; --st)
+        if (st != b0.stages) trial(Shape{b0.w, st, b0.grid});
+      const Shape b1 = best;
+      trial(Shape{b1.w, b1.stages, h->sm_count - h->sm_count / 8});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (failed) {
+      h->ws.upd_w = saved.w;
+      h->ws.tc_stages = saved.stages;
+      h->ws.tc_grid = saved.grid;
+      return OMP_ERR_CUDA;
+    }
     if (cache) {
       if (FILE* f = std::fopen(cache, "a")) {
-        std::fprintf(f, "%s|%d\n", key, best);
+        std::fprintf(f, "%s|%d,%d,%d\n", key, best.w, best.stages, best.grid);
         std::fclose(f);
       }
     }
   }
-  if (best != h->ws.upd_w) {  // captured graphs hold the old launch shape
+  if (best.w != saved.w || best.stages != saved.stages || best.grid != saved.grid ||
+      best.w != h->ws.upd_w || best.stages != h->ws.tc_stages || best.grid != h->ws.tc_grid) {
+    // captured graphs hold the old launch shapes
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
   }
-  h->ws.upd_w = best;
-  if (choice_out) *choice_out = best;
+  h->ws.upd_w = best.w;
+  if (tc) {
+    h->ws.tc_stages = best.stages;
+    h->ws.tc_grid = best.grid;
+  }
+  if (choice_out) *choice_out = best.w;
   return check_launch();
+}
+
+omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* corr_stages, int32_t* corr_ctas) {
+  if (!h) return OMP_ERR_INVALID_ARGUMENT;
+  const bool tc = h->ws.prec != OMP_PREC_FP32;
+  if (update_warps) *update_warps = h->ws.upd_w;
+  if (corr_stages) *corr_stages = tc ? h->ws.tc_stages : 0;
+  if (corr_ctas) *corr_ctas = tc ? h->ws.tc_grid : 0;
+  return OMP_OK;
 }
 
 omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out) {

@@ -9,7 +9,8 @@
 // contiguous range [floor(g T / Geff), floor((g + 1) T / Geff)), Geff = min(grid, T / cmin).
 //
 // Roles (64 + 128 EPI_PARTS threads, one CTA per SM):
-//   warp 0 lane 0  TMA producer, 4 stages of 16 KB (A_op) + 32 KB (B_op)
+//   warp 0 lane 0  TMA producer, NST stages (4 by default; 2 to 4 for the correlation, the
+//                  autotuner's choice) of 16 KB (A_op) + 32 KB (B_op)
 //   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
 //   warps 2..      epilogue, EPI_PARTS warps per TMEM lane quarter (a warp may only read the
 //                  quarter warp % 4), each over EPI_COLS of the unit's 256 columns: tcgen05.ld
@@ -51,8 +52,11 @@ static_assert(THREADS >= EPI_PARTS * BM, "the peer slots are initialised one per
 static_assert(EPI_COLS % 32 == 0, "epilogue chunks are 32 columns");
 constexpr int TMEM_COLS = 2 * BN;
 constexpr int EPI_SCRATCH = EPI_COLS;  // shared floats per epilogue warp
-constexpr int SMEM_BYTES =
-    STAGES * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_SCRATCH * 4 + EPI_PARTS * BM * 8;
+// dynamic shared memory of a mainloop with `nst` operand stages
+__host__ __device__ constexpr int smem_bytes(int nst) {
+  return nst * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_SCRATCH * 4 + EPI_PARTS * BM * 8;
+}
+constexpr int SMEM_BYTES = smem_bytes(STAGES);
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -202,7 +206,7 @@ __device__ __forceinline__ void top8_insert(float (&s)[8], int (&ix)[8], float v
 
 
 // ------------------------------------------------------------------------------- mainloop
-template <int PREC, class Epi>
+template <int PREC, class Epi, int NST = STAGES>
 __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtensorMap* tm_b,
                                           int row_tiles, int col_tiles, int ktiles, int cmin,
                                           unsigned int* err, Epi& epi) {
@@ -221,18 +225,18 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
 
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t bars = base + STAGES * STAGE_BYTES;
+  const uint32_t bars = base + NST * STAGE_BYTES;
   auto full = [&](int s) { return bars + 8u * s; };
-  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
-  auto tfull = [&](int a) { return bars + 8u * (2 * STAGES + a); };
-  auto tempty = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
-  const uint32_t drain = bars + 8u * (2 * STAGES + 4);
+  auto empty = [&](int s) { return bars + 8u * (NST + s); };
+  auto tfull = [&](int a) { return bars + 8u * (2 * NST + a); };
+  auto tempty = [&](int a) { return bars + 8u * (2 * NST + 2 + a); };
+  const uint32_t drain = bars + 8u * (2 * NST + 4);
   uint8_t* bars_gen = smem_raw + (bars - raw);
-  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * STAGES + 5));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * STAGES + 5) + 4);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * NST + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * NST + 5) + 4);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
@@ -265,9 +269,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     // ------------------------------------------------------------------ TMA producer
     int stage = 0;
     uint32_t ph = 0;
-    int last_ph[STAGES];
+    int last_ph[NST];
 #pragma unroll
-    for (int s = 0; s < STAGES; ++s) last_ph[s] = -1;
+    for (int s = 0; s < NST; ++s) last_ph[s] = -1;
     bool ok = true;
     for (int u = u0; u < u1 && ok; ++u) {
       const int s = u / Tn, t = u - s * Tn;
@@ -281,9 +285,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
         tma_load_2d(dst + A_BYTES, tm_b, kc * kelems, t * BN, full(stage));
 #pragma unroll
-        for (int q = 0; q < STAGES; ++q)  // static indices keep last_ph in registers
+        for (int q = 0; q < NST; ++q)  // static indices keep last_ph in registers
           if (q == stage) last_ph[q] = static_cast<int>(ph);
-        if (++stage == STAGES) {
+        if (++stage == NST) {
           stage = 0;
           ph ^= 1u;
         }
@@ -292,7 +296,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     if (!ok) {
       // let every copy this thread issued land before the CTA exits
       volatile int no_abort = 0;
-      for (int s = 0; s < STAGES; ++s)
+      for (int s = 0; s < NST; ++s)
         if (last_ph[s] >= 0) mbar_wait(full(s), static_cast<uint32_t>(last_ph[s]), &no_abort, err);
     }
   } else if (warp == 1 && lane == 0) {
@@ -321,7 +325,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         for (int kk = 0; kk < 4; ++kk)
           mma<PREC>(d, sdesc(a_addr + kk * 32), sdesc(b_addr + kk * 32), (kc | kk) != 0);
         mma_commit(empty(stage));
-        if (++stage == STAGES) {
+        if (++stage == NST) {
           stage = 0;
           ph ^= 1u;
         }
@@ -389,7 +393,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
 // ld: row stride in elements (0 = kelems)
 bool make_kmajor_map(CUtensorMap* m, const void* ptr, int prec, uint64_t rows, uint64_t kelems,
                      uint32_t box_rows, uint64_t ld = 0);
-cudaError_t set_smem_attr(const void* kernel);
+cudaError_t set_smem_attr(const void* kernel, int bytes = SMEM_BYTES);
 
 }  // namespace tcg
 }  // namespace ompk

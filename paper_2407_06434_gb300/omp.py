@@ -38,7 +38,7 @@ EXPORTS = ["omp_desc_default", "omp_create", "omp_destroy", "omp_prepare_diction
            "omp_proposal_baseline_candidates", "omp_solve_batch_candidates",
            "omp_synthesize_signals", "omp_solve_batch_learned", "omp_autotune",
            "omp_loop_passes", "omp_read_bandwidth_probe", "omp_solve_batch_gram",
-           "omp_score_error_bound", "omp_proposal_save", "omp_proposal_load"]
+           "omp_score_error_bound", "omp_proposal_save", "omp_proposal_load", "omp_tuning"]
 NOALLOC_MAX_SIGNALS = 65536
 
 
@@ -118,6 +118,7 @@ def load(path: Optional[str] = None):
         "omp_synthesize_signals": (_I32, [_P, _I64, _I64, _P, _P, _P, _I64, _I32, _P, _P]),
         "omp_solve_batch_learned": (_I32, [_P, _P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
         "omp_autotune": (_I32, [_P, _P, _P, _I64, _I32, _F32, _I32, ctypes.POINTER(_I32), _P]),
+        "omp_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -323,6 +324,13 @@ def omp_autotune(h: Handle, A, Y, S: int, eps: float = 0.0, repeats: int = 2, st
     _check(load().omp_autotune(h.ptr, _ptr(A), _ptr(Y), Y.shape[0], S, eps, repeats,
                                ctypes.byref(c), _stream(stream)), "omp_autotune")
     return c.value
+
+
+def omp_tuning(h: Handle):
+    """(update warps per signal, correlation stages, correlation CTAs) of the handle."""
+    w, st, g = _I32(0), _I32(0), _I32(0)
+    _check(load().omp_tuning(h.ptr, ctypes.byref(w), ctypes.byref(st), ctypes.byref(g)), "omp_tuning")
+    return w.value, st.value, g.value
 
 
 def omp_handle_info(h: Handle):

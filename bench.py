@@ -40,7 +40,8 @@ METRIC = "OMP signals/s, chosen form vs plain FP32 on same GB300 at matched supp
 # entry is removed whenever its kernel changes.
 L2_RESIDENT_BYTES = 64 << 20   # an FP32 dictionary up to half the 129 MB L2 stays resident
 MEASURED_TRAFFIC = {
-    ("gaussian_1024x8192_s32_b4096", "bf16", "correlate"): 25297664.0,
+    ("gaussian_1024x8192_s32_b4096", "bf16", "correlate"): 25296896.0,
+    ("gaussian_1024x8192_s32_b4096", "bf16", "update"): 61878016.0,
 }
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts)
@@ -485,6 +486,7 @@ def run_learned(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = gen.get_config(args.config if args.config != WORKLOAD else "gaussian_1024x8192_s48_b16384")
+    hidden = args.hidden
     A = gen.dictionary(w)
     Y, sp, planted, _ = gen.signals(w, A)
     Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
@@ -492,9 +494,9 @@ def run_learned(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     dense = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
-    p = omp.Proposal(dense.h, hidden=1024, topk=256, max_batch=w.B, train_batch=4096,
-                     pos_weight=float(w.N - w.S) / w.S, lr=1e-3)
-    W1, b1, W2, b2, beta = prop.init_weights(w.N, 1024, w.S, seed=0, M=w.M)
+    p = omp.Proposal(dense.h, hidden=hidden, topk=256, max_batch=w.B, train_batch=4096,
+                     pos_weight=float(w.N - w.S) / w.S, lr=args.train_lr)
+    W1, b1, W2, b2, beta = prop.init_weights(w.N, hidden, w.S, seed=0, M=w.M)
     p.set_weights(*[torch.from_numpy(v).to(dev) for v in (W1, b1, W2, b2, beta)])
     rep = prop.train(dense.h, p, Ad, w, n_signals=args.train_signals, epochs=args.train_epochs,
                      batch=4096, chunk=w.B)
@@ -596,7 +598,10 @@ def run_learned(args):
         "data": "synthetic (seeded Gaussian dictionary, planted sparse signals)",
         "config": {"workload": w.name, "form": "learned proposal (top-256) + BF16 fallback",
                    "M": w.M, "N": w.N, "B": w.B, "S": w.S, "l2": "flushed between timed steps",
-                   "train_signals": args.train_signals, "train_epochs": args.train_epochs},
+                   "train_signals": args.train_signals, "train_epochs": args.train_epochs,
+                   "hidden": hidden, "train_lr": args.train_lr,
+                   "supports": (f"blocks of {w.group} consecutive atoms" if w.group > 1
+                                else "uniform"), "coefficients": w.coef_kind},
         "clocks": clocks,
         "e2e": {"value": w.B * len(e2e) / float(np.sum(e2e)), "unit": "signals/s",
                 "h2d_bytes_per_step": int(Y.nbytes), "d2h_bytes_per_step": int(w.B * w.S * 8)},
@@ -666,6 +671,8 @@ def main():
     ap.add_argument("--form", default="dense", choices=["dense", "learned", "gram"])
     ap.add_argument("--train-signals", type=int, default=1 << 20)
     ap.add_argument("--train-epochs", type=int, default=3)
+    ap.add_argument("--train-lr", type=float, default=1e-3)
+    ap.add_argument("--hidden", type=int, default=1024)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -336,19 +336,28 @@ __device__ __forceinline__ uint32_t orderable(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// SMEM: the row's orderable keys are staged in dynamic shared memory once (N x 4 bytes), so the 33
+// counting passes read shared memory instead of the row in global memory.
+template <bool SMEM>
 __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict__ logits, int N, int K,
                                                          int* __restrict__ out) {
   __shared__ int red[8];
   __shared__ int wcnt_gt[8], wcnt_eq[8];
+  extern __shared__ uint32_t keys_s[];
   const int row = blockIdx.x;
   const float* x = logits + static_cast<size_t>(row) * N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (SMEM) {
+    for (int i = tid; i < N; i += 256) keys_s[i] = orderable(x[i]);
+    __syncthreads();
+  }
+  auto key = [&](int i) -> uint32_t { return SMEM ? keys_s[i] : orderable(x[i]); };
   // bitwise search for the largest threshold T with count(key >= T) >= K
   uint32_t T = 0;
   for (int bit = 31; bit >= 0; --bit) {
     const uint32_t cand = T | (1u << bit);
     int c = 0;
-    for (int i = tid; i < N; i += 256) c += orderable(x[i]) >= cand ? 1 : 0;
+    for (int i = tid; i < N; i += 256) c += key(i) >= cand ? 1 : 0;
     c = warp_sum_int(c);
     if (lane == 0) red[warp] = c;
     __syncthreads();
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict_
   }
   // count elements > T (all kept) and fill with == T in index order
   int ngt = 0;
-  for (int i = tid; i < N; i += 256) ngt += orderable(x[i]) > T ? 1 : 0;
+  for (int i = tid; i < N; i += 256) ngt += key(i) > T ? 1 : 0;
   ngt = warp_sum_int(ngt);
   if (lane == 0) red[warp] = ngt;
   __syncthreads();
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict_
   int* o = out + static_cast<size_t>(row) * K;
   for (int i0 = 0; i0 < N; i0 += 256) {
     const int i = i0 + tid;
-    const uint32_t kv = i < N ? orderable(x[i]) : 0u;
+    const uint32_t kv = i < N ? key(i) : 0u;
     const bool gt = i < N && kv > T;
     const bool eq = i < N && kv == T;
     const unsigned mg = __ballot_sync(0xffffffffu, gt);
@@ -406,6 +415,19 @@ __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict_
     base_eq += te;
     __syncthreads();
   }
+}
+
+// The rows' K largest entries (see topk_rows_kernel); shared-memory keys when a row fits.
+bool launch_topk_rows(const float* logits, int rows, int N, int K, int* out, cudaStream_t s) {
+  const size_t bytes = static_cast<size_t>(N) * 4;
+  if (bytes <= 160 * 1024 &&
+      raise_smem_limit(reinterpret_cast<const void*>(topk_rows_kernel<true>), bytes) == cudaSuccess) {
+    topk_rows_kernel<true><<<rows, 256, bytes, s>>>(logits, N, K, out);
+  } else {
+    cudaGetLastError();
+    topk_rows_kernel<false><<<rows, 256, 0, s>>>(logits, N, K, out);
+  }
+  return cudaGetLastError() == cudaSuccess;
 }
 
 // tau[k] = the q-quantile (the floor(q * n)-th smallest, 0-based) of the positive entries of
@@ -820,8 +842,7 @@ omp_status omp_proposal_infer(omp_proposal p, const float* A, const float* Y, in
   e.beta = p->beta;
   e.out = p->logits;
   if (!gemm(p, p->Hh, b, p->W2b, p->N, p->H, e, s)) return OMP_ERR_CUDA;
-  topk_rows_kernel<<<b, 256, 0, s>>>(p->logits, p->N, p->d.topk, p->cand);
-  bool ok = true;
+  bool ok = launch_topk_rows(p->logits, b, p->N, p->d.topk, p->cand, s);
   if (cand_out)
     ok = ok && cudaMemcpyAsync(cand_out, p->cand, static_cast<size_t>(b) * p->d.topk * 4, cudaMemcpyDefault, s) == cudaSuccess;
   if (logits_out)
@@ -838,8 +859,7 @@ omp_status omp_proposal_baseline_candidates(omp_proposal p, const float* A, cons
   if (!features(p, A, Y, b, false, s)) return OMP_ERR_CUDA;
   const size_t n = static_cast<size_t>(b) * p->N;
   abs_bf16_kernel<<<blocks_for(n), 256, 0, s>>>(p->X, n, p->logits);
-  topk_rows_kernel<<<b, 256, 0, s>>>(p->logits, p->N, p->d.topk, cand_out);
-  return cudaGetLastError() == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
+  return launch_topk_rows(p->logits, b, p->N, p->d.topk, cand_out, s) ? OMP_OK : OMP_ERR_CUDA;
 }
 
 omp_status omp_proposal_set_thresholds(omp_proposal p, const float* tau_host, int32_t S) {
@@ -968,9 +988,10 @@ omp_status omp_proposal_calibrate(omp_proposal p, const float* drops, int64_t B,
 
 omp_status omp_topk_rows(const float* logits, int64_t rows, int64_t N, int32_t K, int32_t* idx_out, void* stream) {
   if (!logits || !idx_out || rows < 1 || N < 1 || K < 1 || K > N || N > (1 << 30)) return OMP_ERR_INVALID_ARGUMENT;
-  topk_rows_kernel<<<static_cast<unsigned>(rows), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      logits, static_cast<int>(N), K, idx_out);
-  return cudaGetLastError() == cudaSuccess ? OMP_OK : OMP_ERR_CUDA;
+  return launch_topk_rows(logits, static_cast<int>(rows), static_cast<int>(N), K, idx_out,
+                          static_cast<cudaStream_t>(stream))
+             ? OMP_OK
+             : OMP_ERR_CUDA;
 }
 
 }  // extern "C"
@@ -987,8 +1008,7 @@ bool proposal_run_inference(omp_proposal p, const float* A, const float* Y, int 
   e.beta = p->beta;
   e.out = p->logits;
   if (!gemm(p, p->Hh, B, p->W2b, p->N, p->H, e, s)) return false;
-  topk_rows_kernel<<<B, 256, 0, s>>>(p->logits, p->N, p->d.topk, p->cand);
-  return cudaGetLastError() == cudaSuccess;
+  return launch_topk_rows(p->logits, B, p->N, p->d.topk, p->cand, s);
 }
 
 // accessors used by the learned solve (runtime.cu)

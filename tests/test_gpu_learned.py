@@ -282,3 +282,55 @@ def test_trained_proposal_against_no_network(lib):
         assert np.linalg.norm(rm["X"][b, :len(s)] - x) <= 1e-4 * np.linalg.norm(x)
     p.close()
     solver.close()
+
+
+def test_trained_proposal_gain_on_grouped_supports(lib):
+    """What the trained network gains over the method without it, where the support distribution
+    has structure to learn: supports of 4 blocks of 4 consecutive atoms (256 x 1024 Gaussian
+    dictionary, S = 16, coefficients |N(0,1)|, noise 1e-3). The network (hidden 512) is trained
+    with the library's kernels on 32768 generated signals labelled by plain OMP, then compared on
+    2048 new signals with the no-network candidates (top-K of |A^T y|, K = 48): its candidates
+    hold more of plain OMP's picks (recall at least 0.15 higher), so fewer signals leave the
+    restricted iteration (fallback rate at least 0.3 lower) and they leave it later. Every result
+    is the least-squares fit on its own support. (On i.i.d. supports, the test above, there is
+    nothing beyond A^T y to learn, and the network only matches the no-network recall.)"""
+    from paper_2407_06434_gb300 import omp, proposal as prop
+    w = gen.get_config("gaussian_64x256_s8_b16", M=256, N=1024, B=2048, S=16, s_min=16,
+                       s_max=16, sigma=1e-3, col_scale=1.0, group=4, coef_kind="abs_normal")
+    A = gen.dictionary(w, seed=21)
+    Ad = dev_dict(A)
+    K, H = 48, 512
+    solver = omp.OmpSolver(w.M, w.N, max_batch=16384, max_iters=w.S, precision="bf16")
+    p = omp.Proposal(solver.h, hidden=H, topk=K, max_batch=w.B, train_batch=1024,
+                     pos_weight=float(w.N - w.S) / w.S, lr=3e-3)
+    W1, b1, W2, b2, beta = prop.init_weights(w.N, H, w.S, seed=0, M=w.M)
+    p.set_weights(cuda(W1), cuda(b1), cuda(W2), cuda(b2), cuda(beta))
+    rep = prop.train(solver.h, p, Ad, w, n_signals=32768, epochs=20, batch=1024, chunk=16384)
+    assert rep.losses[-1] < 0.5 * rep.losses[0]
+    Y, sp, planted, _ = gen.signals(w, A, seed=22)
+    Yd = cuda(Y)
+    X, plain = solver.solve(Ad, Yd, w.S)
+    plain = plain.cpu().numpy()
+    cm = torch.empty((w.B, K), dtype=torch.int32, device="cuda")
+    cb = torch.empty((w.B, K), dtype=torch.int32, device="cuda")
+    p.infer(Ad, Yd, cm)
+    p.baseline_candidates(Ad, Yd, cb)
+    cm, cb = cm.cpu().numpy(), cb.cpu().numpy()
+    rec_m = np.mean([np.isin(plain[b], cm[b]).mean() for b in range(w.B)])
+    rec_b = np.mean([np.isin(plain[b], cb[b]).mean() for b in range(w.B)])
+    rm = _solve_candidates(omp, A, Y, w.S, cm, rep.tau)
+    rb = _solve_candidates(omp, A, Y, w.S, cb, rep.tau)
+    fb_m, fb_b = np.mean(rm["fb"] >= 0), np.mean(rb["fb"] >= 0)
+    step_m = np.mean(np.where(rm["fb"] >= 0, rm["fb"], w.S))
+    step_b = np.mean(np.where(rb["fb"] >= 0, rb["fb"], w.S))
+    print(f"grouped supports: recall {rec_m:.4f} vs {rec_b:.4f}; fallback {fb_m:.4f} vs {fb_b:.4f}; "
+          f"mean fallback step {step_m:.2f} vs {step_b:.2f}; losses {rep.losses[0]:.4f} -> {rep.losses[-1]:.4f}")
+    assert rec_m >= rec_b + 0.15
+    assert fb_m <= fb_b - 0.3
+    assert step_m > step_b
+    for b in range(0, w.B, 61):
+        s = rm["sup"][b][rm["sup"][b] >= 0]
+        x, rn = oracle.replay_support(A, Y[b], s)
+        assert np.linalg.norm(rm["X"][b, :len(s)] - x) <= 1e-4 * np.linalg.norm(x)
+    p.close()
+    solver.close()

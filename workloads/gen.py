@@ -38,12 +38,14 @@ class Workload:
     s_min: int                   # planted sparsity is uniform on [s_min, s_max] (inclusive)
     s_max: int
     dict_kind: str = "gaussian"  # "gaussian" | "coherent"
-    coef_kind: str = "normal"    # "normal" | "signed_uniform"
+    coef_kind: str = "normal"    # "normal" | "signed_uniform" | "abs_normal" (|N(0,1)|)
     sigma: float = 0.0
     eps: float = 0.0             # stop when ||r|| <= eps * ||y|| (relative form)
     precision: str = "fp32"      # correlation precision of the form this workload exercises
     coherence: float = 0.3       # coherent dictionary: squared weight of the shared component
     col_scale: float = 1.0       # Gaussian entries are drawn N(0, col_scale^2) before normalising
+    group: int = 1               # supports are unions of blocks of `group` consecutive atoms
+                                 # (block starts uniform without replacement); 1: plain atoms
 
 
 CONFIGS = {
@@ -72,6 +74,11 @@ CONFIGS = {
     "gaussian_1024x8192_s48_b16384": Workload(
         "gaussian_1024x8192_s48_b16384", M=1024, N=8192, B=16384, S=48, s_min=48, s_max=48,
         sigma=1e-3, precision="bf16"),
+    # the learned-proposal workload with a support prior a network can learn: supports are 12
+    # blocks of 4 consecutive atoms, coefficients |N(0,1)| (nonnegative sparse coding)
+    "grouped_1024x8192_s48_g4_b16384": Workload(
+        "grouped_1024x8192_s48_g4_b16384", M=1024, N=8192, B=16384, S=48, s_min=48, s_max=48,
+        sigma=1e-3, precision="bf16", group=4, coef_kind="abs_normal"),
     # the paper's three application shapes (Table tab:realistic), filled with synthetic data
     "patches_256x1024_s32_b5000": Workload(
         "patches_256x1024_s32_b5000", M=256, N=1024, B=5000, S=32, s_min=32, s_max=32,
@@ -124,8 +131,11 @@ def planted(w: Workload, seed: int = 0):
     """Planted supports and coefficients for the whole batch.
 
     Returns (sparsity[B] int32, support[B, s_max] int64 padded with -1, coef[B, s_max] float64
-    padded with 0). Supports are uniform without replacement over the N atoms.
+    padded with 0). Supports are uniform without replacement over the N atoms, or, with
+    ``group`` g > 1, s / g blocks of g consecutive atoms chosen uniformly without replacement
+    among the N / g blocks (a support prior a proposal network can learn).
     """
+    g = _check_group(w)
     if w.s_min == w.s_max:
         sp = np.full(w.B, w.s_max, dtype=np.int32)
     else:
@@ -133,7 +143,11 @@ def planted(w: Workload, seed: int = 0):
     srng = _rng(seed, _S_SUPPORT)
     sup = np.full((w.B, w.s_max), -1, dtype=np.int64)
     for b in range(w.B):
-        sup[b, : sp[b]] = srng.choice(w.N, size=int(sp[b]), replace=False)
+        if g == 1:
+            sup[b, : sp[b]] = srng.choice(w.N, size=int(sp[b]), replace=False)
+        else:
+            blocks = srng.choice(w.N // g, size=int(sp[b]) // g, replace=False)
+            sup[b, : sp[b]] = (blocks[:, None] * g + np.arange(g)).reshape(-1)
     crng = _rng(seed, _S_COEF)
     if w.coef_kind == "normal":
         coef = crng.standard_normal((w.B, w.s_max))
@@ -141,10 +155,19 @@ def planted(w: Workload, seed: int = 0):
         mag = crng.uniform(0.5, 1.0, size=(w.B, w.s_max))
         sign = np.where(crng.integers(0, 2, size=(w.B, w.s_max)) == 0, -1.0, 1.0)
         coef = mag * sign
+    elif w.coef_kind == "abs_normal":
+        coef = np.abs(crng.standard_normal((w.B, w.s_max)))
     else:
         raise ValueError(w.coef_kind)
     coef[np.arange(w.s_max)[None, :] >= sp[:, None]] = 0.0
     return sp, sup, coef
+
+
+def _check_group(w: Workload) -> int:
+    g = int(w.group)
+    if g < 1 or w.N % g or w.s_min % g or w.s_max % g:
+        raise ValueError("group must divide N and the sparsities")
+    return g
 
 
 def _noise_rows(w: Workload, seed: int, lo: int, hi: int) -> np.ndarray:
@@ -196,15 +219,18 @@ def training_batch(w: Workload, n: int, chunk_id: int, seed: int = 0):
 
     Returns (support int32 n x s_max (-1 padded), coef float32 n x s_max, noise float32 n x M).
     Supports are uniform without replacement: the first s distinct values of a row of uniform
-    draws, which is a uniform random s-subset in random order."""
+    draws, which is a uniform random s-subset in random order (of blocks of ``group`` consecutive
+    atoms when group > 1)."""
     rng = _rng(seed, _S_TRAIN, chunk_id)
+    g = _check_group(w)
     s_max = w.s_max
     if w.s_min == w.s_max:
         sp = np.full(n, s_max, dtype=np.int32)
     else:
-        sp = rng.integers(w.s_min, w.s_max + 1, size=n).astype(np.int32)
-    m = s_max + 32
-    draws = rng.integers(0, w.N, size=(n, m))
+        sp = rng.integers(w.s_min // g, w.s_max // g + 1, size=n).astype(np.int32) * g
+    nb, s_b = w.N // g, s_max // g      # draw blocks (atoms when g = 1)
+    m = s_b + 32
+    draws = rng.integers(0, nb, size=(n, m))
     order = np.argsort(draws, axis=1, kind="stable")
     srt = np.take_along_axis(draws, order, axis=1)
     dup_sorted = np.zeros_like(srt, dtype=bool)
@@ -213,13 +239,16 @@ def training_batch(w: Workload, n: int, chunk_id: int, seed: int = 0):
     np.put_along_axis(dup, order, dup_sorted, axis=1)
     keep = ~dup
     rank = np.cumsum(keep, axis=1)
-    if np.any(rank[:, -1] < s_max):
+    if np.any(rank[:, -1] < s_b):
         raise RuntimeError("too many repeated draws; enlarge the draw width")
-    sel = keep & (rank <= s_max)
-    sup = draws[sel].reshape(n, s_max).astype(np.int32)
+    sel = keep & (rank <= s_b)
+    blocks = draws[sel].reshape(n, s_b)
+    sup = (blocks[:, :, None] * g + np.arange(g)).reshape(n, s_max).astype(np.int32)
     sup[np.arange(s_max)[None, :] >= sp[:, None]] = -1
     if w.coef_kind == "normal":
         coef = rng.standard_normal((n, s_max), dtype=np.float32)
+    elif w.coef_kind == "abs_normal":
+        coef = np.abs(rng.standard_normal((n, s_max), dtype=np.float32))
     else:
         coef = rng.uniform(0.5, 1.0, size=(n, s_max)).astype(np.float32)
         coef *= np.where(rng.integers(0, 2, size=coef.shape) == 0, -1.0, 1.0).astype(np.float32)

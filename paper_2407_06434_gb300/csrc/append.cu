@@ -77,6 +77,7 @@ struct GroupSmem {
   int* scal;     // 4: n*, dependent flag, rescoring skipped, candidates to rescore
   float* top2;   // 2: the merged lists' best and second-best quantised scores
   float* rinv;   // 2: inverse norms of the two best merged candidates (threshold on)
+  float* cq;     // 8: the merged candidates' quantised scores, best first
   float* rows;   // 2 x Mp when the threshold is on: FP32 rows of the two best merged candidates
   float* tri;    // Smax (Smax + 1) / 2 when Smax <= kTriMax: staged copy of the packed FP32 F
 };
@@ -93,7 +94,7 @@ __host__ __device__ __forceinline__ size_t row_floats(const Ws& ws) {
 __host__ __device__ __forceinline__ size_t group_bytes(const Ws& ws) {
   const int Smax = ws.Smax;
   const size_t b = static_cast<size_t>(Smax + 1) * 8 + static_cast<size_t>(Smax) * 8 + 64 * 4 +
-                   8 * 4 + 16 * 4 + 16 + 8 + 8 + row_floats(ws) * 4 +
+                   8 * 4 + 16 * 4 + 16 + 8 + 8 + 8 * 4 + row_floats(ws) * 4 +
                    (tri_floats(Smax) * 4 + 15) / 16 * 16;
   return (b + 15) / 16 * 16;
 }
@@ -116,6 +117,7 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* base, int grp, co
   s.z = s.w + Smax;
   s.top2 = s.z + Smax;
   s.rinv = s.top2 + 2;
+  s.cq = s.rinv + 2;
   return s;
 }
 
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
             }
         }
         if (lane == 0) gs.cidx[sel] = (g_i >= 0 && g_i < ws.N) ? g_i : -1;
+        if (lane == 0) gs.cq[sel] = g_s;
         if (lane == 0 && sel < 2) gs.top2[sel] = g_s;
         if (sel == 0)
           s_first = g_s;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
     }
     group_sync(W, grp);
     const bool skip = gs.scal[2] != 0;
-    const int nres = gs.scal[3];
+    int nres = gs.scal[3];
     if (ws.tau) {
       // the two best merged candidates' FP32 rows and inverse norms, for the next step's
       // threshold: copied to shared memory in the background (each warp its own slots), read at
@@ -426,8 +429,16 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
       cp_async_commit();
     }
     // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
-    // candidates per pass so their row loads are in flight together
+    // candidates per pass so their row loads are in flight together. With the bound, a pass
+    // starts only if its first candidate (they come best first) could still beat the best FP32
+    // score found so far: one whose quantised score is more than eps_k ||r|| below that has an
+    // FP32 score strictly below it, and so have all that follow.
+    const float qsr = ws.prec == OMP_PREC_FP8_E4M3 ? ws.sr[k & 1][p] : 1.f;
+    const bool adapt = ws.rescore_eps > 0.f && rprev > 1e-30f && qsr > 0.f;
+    float tmax = -1.f;
+    int ndone = 0;
     for (int c = 0; !skip && c < nres; c += 2) {
+      if (adapt && c > 0 && !(gs.cq[c] >= (tmax - eps_k * rprev) / qsr)) break;
       const int n0 = gs.cidx[c];
       const int n1 = c + 1 < nres ? gs.cidx[c + 1] : -1;
       const float4* a0 = reinterpret_cast<const float4*>(ws.A32 + static_cast<size_t>(n0 < 0 ? 0 : n0) * ws.Mp);
@@ -449,7 +460,19 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
         gs.cpart[c * 8 + wig] = acc0;
         if (c + 1 < nres) gs.cpart[(c + 1) * 8 + wig] = acc1;
       }
+      ndone = c + 2 < nres ? c + 2 : nres;
+      if (adapt && ndone < nres) {  // the pass's FP32 scores (every thread, from the partials)
+        group_sync(W, grp);
+        for (int cc = c; cc < ndone; ++cc) {
+          const int n = gs.cidx[cc];
+          if (n < 0) continue;
+          float v = 0.f;
+          for (int w = 0; w < W; ++w) v += gs.cpart[cc * 8 + w];
+          tmax = fmaxf(tmax, fabsf(v) * __ldg(ws.inv_norm + n));
+        }
+      }
     }
+    if (!skip) nres = ndone;  // the candidates not rescored cannot beat the best that was
     group_sync(W, grp);
     if (wig == 0 && skip) {
       if (lane == 0) gs.scal[0] = gs.cidx[0];

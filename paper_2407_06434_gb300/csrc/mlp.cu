@@ -63,27 +63,35 @@ struct EpiAct {
     const int cb = t * BN + c0;
     const bool rok = r < rows;
     const float rs = (rok && rowscale) ? rowscale[r] : 1.f;
-    __align__(16) __nv_bfloat16 ob[32];
+    uint32_t ow[16];  // the 32 BF16 results, two per word (kept in registers)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = cb + j;
-      float x = __uint_as_float(v[j]) * rs;
-      if (c < cols) {
-        if (colscale) x *= __ldg(colscale + c);
-        if (bias) x += __ldg(bias + c);
+    for (int j = 0; j < 32; j += 2) {
+      float y2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = cb + j + e;
+        float x = __uint_as_float(v[j + e]) * rs;
+        if (c < cols) {
+          if (colscale) x *= __ldg(colscale + c);
+          if (bias) x += __ldg(bias + c);
+        }
+        if (rok && c < cols && pre) pre[static_cast<size_t>(r) * cols + c] = x;
+        y2[e] = gelu ? gelu_f(x) : x;
+        if (outT && c < cols && rok) outT[static_cast<size_t>(c) * ldT + r] = __float2bfloat16_rn(y2[e]);
       }
-      if (rok && c < cols && pre) pre[static_cast<size_t>(r) * cols + c] = x;
-      const float y = gelu ? gelu_f(x) : x;
-      ob[j] = __float2bfloat16_rn(y);
-      if (outT && c < cols && rok) outT[static_cast<size_t>(c) * ldT + r] = ob[j];
+      const __nv_bfloat162 h = __floats2bfloat162_rn(y2[0], y2[1]);
+      ow[j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
     }
     if (!rok) return;
     __nv_bfloat16* dst = out + static_cast<size_t>(r) * cols + cb;
     if (cb + 32 <= cols && (cols & 7) == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<uint4*>(dst)[q] = reinterpret_cast<const uint4*>(ob)[q];
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<uint4*>(dst)[q] = make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]);
     } else {
-      for (int j = 0; j < 32 && cb + j < cols; ++j) dst[j] = ob[j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (cb + j < cols) dst[j] = __ushort_as_bfloat16(static_cast<unsigned short>((j & 1) ? (ow[j >> 1] >> 16) : (ow[j >> 1] & 0xFFFFu)));
     }
   }
   __device__ void end(bool) {}
@@ -110,18 +118,41 @@ struct EpiF32 {
     const int cb = t * BN + c0;
     const float bt = skipX ? *beta : 0.f;
     float* dst = out + static_cast<size_t>(r) * cols + cb;
-    if (cb + 32 <= cols && (cols & 3) == 0) {
+    if (cb + 32 <= cols && (cols & 7) == 0) {
+      // the row's 32 skip features in four 16-byte loads (cols a multiple of 8 keeps them
+      // aligned), the bias once per column
+      uint32_t xw[16];  // 32 BF16 values, two per word (a BF16 is the top half of an FP32)
+      if (skipX) {
+        const uint4* src = reinterpret_cast<const uint4*>(skipX + static_cast<size_t>(r) * cols + cb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 u = __ldg(src + q);
+          xw[4 * q] = u.x;
+          xw[4 * q + 1] = u.y;
+          xw[4 * q + 2] = u.z;
+          xw[4 * q + 3] = u.w;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        float4 o;
-        o.x = val(v, 4 * q + 0, r, cb + 4 * q + 0, bt);
-        o.y = val(v, 4 * q + 1, r, cb + 4 * q + 1, bt);
-        o.z = val(v, 4 * q + 2, r, cb + 4 * q + 2, bt);
-        o.w = val(v, 4 * q + 3, r, cb + 4 * q + 3, bt);
-        reinterpret_cast<float4*>(dst)[q] = o;
+        float ov[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * q + e;
+          float o = __uint_as_float(v[j]) + (bias ? __ldg(bias + cb + j) : 0.f);
+          if (skipX) {
+            const uint32_t wd = xw[j >> 1];
+            const float xf = __uint_as_float((j & 1) ? (wd & 0xFFFF0000u) : (wd << 16));
+            o = fmaf(bt, fabsf(xf), o);
+          }
+          ov[e] = o;
+        }
+        reinterpret_cast<float4*>(dst)[q] = make_float4(ov[0], ov[1], ov[2], ov[3]);
       }
     } else {
-      for (int j = 0; j < 32 && cb + j < cols; ++j) dst[j] = val(v, j, r, cb + j, bt);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (cb + j < cols) dst[j] = val(v, j, r, cb + j, bt);
     }
   }
   __device__ void end(bool) {}
@@ -352,20 +383,71 @@ __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict_
     __syncthreads();
   }
   auto key = [&](int i) -> uint32_t { return SMEM ? keys_s[i] : orderable(x[i]); };
-  // bitwise search for the largest threshold T with count(key >= T) >= K
+  // T = the K-th largest key: the largest threshold with count(key >= T) >= K
   uint32_t T = 0;
-  for (int bit = 31; bit >= 0; --bit) {
-    const uint32_t cand = T | (1u << bit);
-    int c = 0;
-    for (int i = tid; i < N; i += 256) c += key(i) >= cand ? 1 : 0;
-    c = warp_sum_int(c);
-    if (lane == 0) red[warp] = c;
-    __syncthreads();
-    int tot = 0;
+  if (SMEM) {
+    // radix select, 8 bits a pass from the top: a 256-bin histogram of the keys that share the
+    // bits fixed so far (warp-aggregated shared-memory atomics), then the bin that holds the
+    // K-th largest of them
+    __shared__ int hist[256];
+    __shared__ uint32_t sel_s[2];  // the bin found, the rank still to find within it
+    uint32_t fixed = 0;            // mask of the bits of T fixed so far
+    int rem = K;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      hist[tid] = 0;
+      __syncthreads();
+      for (int i0 = 0; i0 < N; i0 += 256) {
+        const int i = i0 + tid;
+        const uint32_t kv = i < N ? keys_s[i] : 0u;
+        const bool in = i < N && (kv & fixed) == T;
+        const int bin = in ? static_cast<int>((kv >> shift) & 255u) : 256;
+        const unsigned same = __match_any_sync(0xffffffffu, bin);
+        if (in && lane == __ffs(same) - 1) atomicAdd(&hist[bin], __popc(same));
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // lane l owns bins 8l .. 8l + 7; counts above a bin come from the higher lanes
+        int cnt[8], tot = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) tot += red[w];
-    __syncthreads();
-    if (tot >= K) T = cand;
+        for (int j = 0; j < 8; ++j) {
+          cnt[j] = hist[8 * lane + j];
+          tot += cnt[j];
+        }
+        int above = 0;  // keys in the bins of the lanes above this one
+        for (int l2 = 31; l2 > 0; --l2) {
+          const int t2 = __shfl_sync(0xffffffffu, tot, l2);
+          if (l2 > lane) above += t2;
+        }
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+          if (above < rem && above + cnt[j] >= rem) {
+            sel_s[0] = static_cast<uint32_t>(8 * lane + j);
+            sel_s[1] = static_cast<uint32_t>(rem - above);
+          }
+          above += cnt[j];
+        }
+      }
+      __syncthreads();
+      T |= sel_s[0] << shift;
+      fixed |= 255u << shift;
+      rem = static_cast<int>(sel_s[1]);
+      __syncthreads();
+    }
+  } else {
+    // bitwise search over the row in global memory
+    for (int bit = 31; bit >= 0; --bit) {
+      const uint32_t cand = T | (1u << bit);
+      int c = 0;
+      for (int i = tid; i < N; i += 256) c += key(i) >= cand ? 1 : 0;
+      c = warp_sum_int(c);
+      if (lane == 0) red[warp] = c;
+      __syncthreads();
+      int tot = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      __syncthreads();
+      if (tot >= K) T = cand;
+    }
   }
   // count elements > T (all kept) and fill with == T in index order
   int ngt = 0;

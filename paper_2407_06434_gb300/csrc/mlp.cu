@@ -188,30 +188,39 @@ struct EpiBCE {
     const int cb = t * BN + c0;
     const uint32_t bits = (rok && cb < cols) ? labels[static_cast<size_t>(r) * (cols >> 5) + (cb >> 5)] : 0u;
     const float bt = *beta;
-    __align__(16) __nv_bfloat16 ob[32];
+    uint32_t ow[16];  // the 32 BF16 gradients, two per word (kept in registers)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = cb + j;
-      const bool ok = rok && c < cols;
-      const float ax = ok ? fabsf(__bfloat162float(skipX[static_cast<size_t>(r) * cols + c])) : 0.f;
-      const float o = fmaf(bt, ax, __uint_as_float(v[j]) + (c < cols ? __ldg(bias + c) : 0.f));
-      const float y = ((bits >> j) & 1u) ? 1.f : 0.f;
-      const float sg = 1.f / (1.f + expf(-o));
-      const float g = (sg * (1.f - y + pos_weight * y) - pos_weight * y) * inv_count;
-      if (ok) {
-        lsum += (pos_weight * y * softplus_f(-o) + (1.f - y) * softplus_f(o)) * inv_count;
-        bsum = fmaf(g, ax, bsum);
+    for (int j = 0; j < 32; j += 2) {
+      float g2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = cb + j + e;
+        const bool ok = rok && c < cols;
+        const float ax = ok ? fabsf(__bfloat162float(skipX[static_cast<size_t>(r) * cols + c])) : 0.f;
+        const float o = fmaf(bt, ax, __uint_as_float(v[j + e]) + (c < cols ? __ldg(bias + c) : 0.f));
+        const float y = ((bits >> (j + e)) & 1u) ? 1.f : 0.f;
+        const float sg = 1.f / (1.f + expf(-o));
+        const float g = (sg * (1.f - y + pos_weight * y) - pos_weight * y) * inv_count;
+        if (ok) {
+          lsum += (pos_weight * y * softplus_f(-o) + (1.f - y) * softplus_f(o)) * inv_count;
+          bsum = fmaf(g, ax, bsum);
+        }
+        g2[e] = ok ? g : 0.f;
+        if (ok) dOT[static_cast<size_t>(c) * ldT + r] = __float2bfloat16_rn(g2[e]);
       }
-      ob[j] = __float2bfloat16_rn(ok ? g : 0.f);
-      if (ok) dOT[static_cast<size_t>(c) * ldT + r] = ob[j];
+      const __nv_bfloat162 h = __floats2bfloat162_rn(g2[0], g2[1]);
+      ow[j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
     }
     if (!rok) return;
     __nv_bfloat16* dst = dO + static_cast<size_t>(r) * cols + cb;
     if (cb + 32 <= cols) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<uint4*>(dst)[q] = reinterpret_cast<const uint4*>(ob)[q];
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<uint4*>(dst)[q] = make_uint4(ow[4 * q], ow[4 * q + 1], ow[4 * q + 2], ow[4 * q + 3]);
     } else {
-      for (int j = 0; j < 32 && cb + j < cols; ++j) dst[j] = ob[j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (cb + j < cols) dst[j] = __ushort_as_bfloat16(static_cast<unsigned short>((j & 1) ? (ow[j >> 1] >> 16) : (ow[j >> 1] & 0xFFFFu)));
     }
   }
   __device__ void end(bool) {
@@ -449,53 +458,52 @@ __global__ void __launch_bounds__(256) topk_rows_kernel(const float* __restrict_
       if (tot >= K) T = cand;
     }
   }
-  // count elements > T (all kept) and fill with == T in index order
-  int ngt = 0;
-  for (int i = tid; i < N; i += 256) ngt += key(i) > T ? 1 : 0;
-  ngt = warp_sum_int(ngt);
-  if (lane == 0) red[warp] = ngt;
+  // Output: the > T elements and the first K - count(> T) elements == T, in index order. Each
+  // warp owns a contiguous index range: one pass counts its > T and == T elements, one barrier
+  // gives every warp the counts of the ranges before it, and each warp then writes its selected
+  // indices in order (ballots within the warp, no further barriers).
+  const int per = (N + 7) / 8;
+  const int lo = min(N, warp * per), hi = min(N, lo + per);
+  int cg = 0, ce = 0;
+  for (int i = lo + lane; i < hi; i += 32) {
+    const uint32_t kv = key(i);
+    cg += kv > T ? 1 : 0;
+    ce += kv == T ? 1 : 0;
+  }
+  cg = warp_sum_int(cg);
+  ce = warp_sum_int(ce);
+  if (lane == 0) {
+    wcnt_gt[warp] = cg;
+    wcnt_eq[warp] = ce;
+  }
   __syncthreads();
-  int total_gt = 0;
+  int total_gt = 0, base_gt = 0, base_eq = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) total_gt += red[w];
+  for (int w = 0; w < 8; ++w) {
+    total_gt += wcnt_gt[w];
+    if (w < warp) {
+      base_gt += wcnt_gt[w];
+      base_eq += wcnt_eq[w];
+    }
+  }
   const int need_eq = K - total_gt;
-  __syncthreads();
-  // ordered pass over chunks of 256 indices: block-wide exclusive scans of the two counts
-  int base_gt = 0, base_eq = 0;
   int* o = out + static_cast<size_t>(row) * K;
-  for (int i0 = 0; i0 < N; i0 += 256) {
-    const int i = i0 + tid;
-    const uint32_t kv = i < N ? key(i) : 0u;
-    const bool gt = i < N && kv > T;
-    const bool eq = i < N && kv == T;
+  const unsigned below = (1u << lane) - 1u;
+  for (int i0 = lo; i0 < hi; i0 += 32) {
+    const int i = i0 + lane;
+    const uint32_t kv = i < hi ? key(i) : 0u;
+    const bool gt = i < hi && kv > T;
+    const bool eq = i < hi && kv == T;
     const unsigned mg = __ballot_sync(0xffffffffu, gt);
     const unsigned me = __ballot_sync(0xffffffffu, eq);
-    if (lane == 0) {
-      wcnt_gt[warp] = __popc(mg);
-      wcnt_eq[warp] = __popc(me);
-    }
-    __syncthreads();
-    int pg = 0, pe = 0, tg = 0, te = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      if (w < warp) {
-        pg += wcnt_gt[w];
-        pe += wcnt_eq[w];
-      }
-      tg += wcnt_gt[w];
-      te += wcnt_eq[w];
-    }
-    const unsigned below = (1u << lane) - 1u;
-    const int rg = base_gt + pg + __popc(mg & below);
-    const int re = base_eq + pe + __popc(me & below);
-    // slots: the > T elements and the first need_eq == T elements, merged in index order
+    const int rg = base_gt + __popc(mg & below);
+    const int re = base_eq + __popc(me & below);
     if (gt || (eq && re < need_eq)) {
       const int slot = rg + min(re, need_eq);
       if (slot < K) o[slot] = i;
     }
-    base_gt += tg;
-    base_eq += te;
-    __syncthreads();
+    base_gt += __popc(mg);
+    base_eq += __popc(me);
   }
 }
 

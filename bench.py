@@ -220,6 +220,7 @@ def run_gpu(args):
         sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
         omp.omp_prepare_dictionary(h, Ad)
         tuned = omp.omp_autotune(h, Ad, Yd, w.S, w.eps, repeats=2)
+        shapes = omp.omp_tuning(h)
         for _ in range(args.warmup):
             omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
         torch.cuda.synchronize()
@@ -267,7 +268,7 @@ def run_gpu(args):
         # one more solve, untimed, with the per-signal diagnostics the error report uses
         Xd, Sd, nd, rd, _ = solver.solve(Ad, Yd, w.S, w.eps, diagnostics=True)
         torch.cuda.synchronize()
-        res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live, update_warps=tuned,
+        res = dict(total_ms=total, ms=ms, corr=corr, upd=upd, live=live, update_warps=tuned, shapes=shapes,
                    e2e_s=float(np.sum(e2e_t)), e2e_steps=len(e2e_t),
                    sup=Sd.cpu().numpy(), X=Xd.cpu().numpy(), n_iter=nd.cpu().numpy(),
                    resid=rd.cpu().numpy())
@@ -352,6 +353,9 @@ def run_gpu(args):
         "config": {"workload": w.name, "M": w.M, "N": w.N, "B": w.B, "S": w.S,
                    "precision": args.precision, "rescore_topk": topk,
                    "update_warps_per_signal": chosen["update_warps"],
+                   "update_persistent": bool(chosen["shapes"][1]),
+                   "correlation_stages": chosen["shapes"][2] or None,
+                   "correlation_ctas": chosen["shapes"][3] or None,
                    "update_gather": "24-bit copy of A (3 bytes an element)" if args.gather24
                    else "FP32 rows",
                    "l2": "flushed between timed steps (512 MiB write)",

@@ -200,18 +200,22 @@ omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, i
  * solves of (A, Y, B, S, eps) for each valid launch shape and keeps the fastest on the handle:
  * first the append/update kernel's warps per signal (1, 2, 4 or 8 for the padded signal length),
  * then, on the tensor-core paths, the correlation's pipeline depth (2, 3 or 4 operand stages of
- * 48 KB) and its persistent grid (every SM, or seven eighths of them). *choice_out (may be NULL)
- * receives the warps per signal; omp_tuning reads all three. If the environment variable
- * OMP_AUTOTUNE_CACHE names a file, a choice recorded there for the same GPU, M, N, precision, B
- * and S is used without timing ("key|warps,stages,ctas" lines; a line with warps only keeps the
- * correlation's current shape), and new choices are appended to it. Synchronises `stream`.
- * Captured graphs are dropped when the choice changes. */
+ * 48 KB) and its persistent grid (every SM, or seven eighths of them), then the update kernel's
+ * persistent form (a grid of the blocks that fit on the GPU taking positions from a counter)
+ * against one block per signal. *choice_out (may be NULL) receives the warps per signal;
+ * omp_tuning reads all four. If the environment variable OMP_AUTOTUNE_CACHE names a file, a
+ * choice recorded there for the same GPU, M, N, precision, B and S is used without timing
+ * ("key|warps,stages,ctas,persistent" lines; shorter lines keep the other shapes), and new
+ * choices are appended to it. Synchronises `stream`. Captured graphs are dropped when the choice
+ * changes. */
 omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B, int32_t S, float eps,
                         int32_t repeats, int32_t* choice_out, void* stream);
 
-/* The handle's current launch shapes: update warps per signal, correlation operand stages and
- * persistent CTAs (the last two 0 on the FP32 path). Host only. */
-omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* corr_stages, int32_t* corr_ctas);
+/* The handle's current launch shapes (each pointer may be NULL): update warps per signal, update
+ * persistent form (0 or 1), correlation operand stages and persistent CTAs (the last two 0 on the
+ * FP32 path). Host only. */
+omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* update_persistent,
+                      int32_t* corr_stages, int32_t* corr_ctas);
 
 /* The descriptor the handle was created with (after defaults) and the device's SM count. */
 omp_status omp_handle_info(omp_handle h, omp_desc* desc_out, int32_t* sm_count_out);

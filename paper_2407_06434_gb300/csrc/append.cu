@@ -261,19 +261,16 @@ __device__ __forceinline__ float4 widen(const Slot4<G24>& r) {
   }
 }
 
+// One step of the signal at live position p (p < L), by the block's W warps; every return is
+// taken by the whole block.
 template <int W, int V, bool G24>
-__global__ void __launch_bounds__(W * 32, 16 / W)
-    append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
-  k = iter_of(ws, k);
+__device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int p, int S, float eps,
+                                                int eps_rel, unsigned char* smem) {
   const bool top1 = ws.prec == OMP_PREC_FP32;
   const int lane = threadIdx.x & 31;
   const int grp = 0, wig = threadIdx.x >> 5;
-  const int L = ws.cnt[k + 1];
-  const int p = blockIdx.x;
-  if (p >= L) return;  // the whole group leaves together
   const int id = ws.live[k & 1][p];
   const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
-  extern __shared__ __align__(16) unsigned char smem[];
   GroupSmem gs = group_smem(smem, grp, ws);
 
   // The candidate lists head the critical path (merge, rescoring, append), so their loads are
@@ -774,14 +771,69 @@ __global__ void __launch_bounds__(W * 32, 16 / W)
   }
 }
 
+// The append/update kernel. Either one block per live position (grid = B), or persistent
+// (ws.upd_persist): a grid of as many blocks as fit on the GPU, each taking the next position
+// from the iteration's counter until none is left, so blocks stay resident across signals and a
+// block whose signal finishes early (the rescoring skipped, a retirement) takes another.
+template <int W, int V, bool G24>
+__global__ void __launch_bounds__(W * 32, 16 / W)
+    append_update_kernel(Ws ws, int k, int S, float eps, int eps_rel) {
+  k = iter_of(ws, k);
+  const int L = ws.cnt[k + 1];
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!ws.upd_persist) {
+    if (static_cast<int>(blockIdx.x) < L)
+      update_position<W, V, G24>(ws, k, L, blockIdx.x, S, eps, eps_rel, smem);
+    return;
+  }
+  __shared__ int next_p;
+  for (;;) {
+    if (threadIdx.x == 0) next_p = atomicAdd(ws.upd_ctr + k, 1);
+    __syncthreads();
+    const int p = next_p;
+    __syncthreads();  // every thread has read it before the next position is taken
+    if (p >= L) break;
+    update_position<W, V, G24>(ws, k, L, p, S, eps, eps_rel, smem);
+  }
+}
+
+// resident blocks of one append/update kernel variant on the device (0 if the query fails)
+template <int W, int V, bool G24>
+int resident_blocks(size_t smem) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, append_update_kernel<W, V, G24>, W * 32, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb * sms;
+}
+
 // W warps per signal and V float4 slots per lane cover Mp <= 128 W V.
+template <int W, int V, bool G24>
+void launch_g(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  const size_t smem = group_bytes(ws);
+  int grid = B;
+  if (ws.upd_persist) {
+    const int r = resident_blocks<W, V, G24>(smem);
+    if (r > 0 && r < grid) grid = r;
+  }
+  append_update_kernel<W, V, G24><<<grid, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
+}
+
 template <int W, int V>
 void launch_t(const Ws& ws, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
-  const size_t smem = group_bytes(ws);
   if (ws.A24h)
-    append_update_kernel<W, V, true><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
+    launch_g<W, V, true>(ws, k, B, S, eps, eps_rel, s);
   else
-    append_update_kernel<W, V, false><<<B, W * 32, smem, s>>>(ws, k, S, eps, eps_rel);
+    launch_g<W, V, false>(ws, k, B, S, eps, eps_rel, s);
 }
 
 template <int W>

@@ -64,6 +64,8 @@ struct Ws {
   int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
   int tc_stages;   // operand stages of the correlation's pipeline (2..4; autotuned)
   int upd_w;       // append/update kernel: warps per signal (1, 2, 4, 8; autotuned)
+  int upd_persist; // append/update kernel: persistent grid taking positions from upd_ctr (autotuned)
+  int* upd_ctr;    // Smax + 1 per-iteration position counters of the persistent form (zeroed by init)
   int64_t Fstride; // Smax (Smax + 1) / 2 rounded up to a multiple of 4
   // dictionary
   float* A32;

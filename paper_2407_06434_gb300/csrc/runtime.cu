@@ -419,6 +419,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
          (ws.prec != OMP_PREC_FP8_E4M3 || dalloc(h, &ws.ea, 1));
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
+  ok = ok && dalloc(h, &ws.upd_ctr, Sm + 1);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&
        dalloc(h, &ws.F32, Bm * static_cast<size_t>(ws.Fstride)) && dalloc(h, &ws.bv, Bm * Sm) &&
        dalloc(h, &ws.sup, Bm * Sm);
@@ -643,23 +644,23 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   const bool tc = h->ws.prec != OMP_PREC_FP32;
   // a launch shape: update warps per signal, correlation stages and persistent CTAs
   struct Shape {
-    int w, stages, grid;
+    int w, stages, grid, persist;
   };
   auto valid = [&](const Shape& c) {
     return update_slots(h->ws.Mp, c.w) != 0 &&
            (!tc || (c.stages >= 2 && c.stages <= 4 && c.grid >= 1 && c.grid <= h->sm_count));
   };
-  const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid};
-  Shape best{0, saved.stages, saved.grid};
-  if (cache) {  // a previous run's choice for the same key: "key|w" or "key|w,stages,grid"
+  const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid, h->ws.upd_persist};
+  Shape best{0, saved.stages, saved.grid, saved.persist};
+  if (cache) {  // a previous run's choice: "key|w", "key|w,stages,grid" or "key|w,stages,grid,persist"
     if (FILE* f = std::fopen(cache, "r")) {
       char line[512];
       while (std::fgets(line, sizeof(line), f)) {
         char* bar = std::strrchr(line, '|');
         Shape c = saved;
-        const int n = bar ? std::sscanf(bar + 1, "%d,%d,%d", &c.w, &c.stages, &c.grid) : 0;
+        const int n = bar ? std::sscanf(bar + 1, "%d,%d,%d,%d", &c.w, &c.stages, &c.grid, &c.persist) : 0;
         if (std::strncmp(line, key, std::strlen(key)) == 0 && line[std::strlen(key)] == '|' &&
-            (n == 1 || n == 3) && valid(c))
+            (n == 1 || n == 3 || n == 4) && valid(c) && (c.persist == 0 || c.persist == 1))
           best = c;
       }
       std::fclose(f);
@@ -682,6 +683,7 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       h->ws.upd_w = c.w;
       h->ws.tc_stages = c.stages;
       h->ws.tc_grid = c.grid;
+      h->ws.upd_persist = c.persist;
       launch_set_args(h->args_dev, a, s);
       enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);  // warm-up
       cudaEventRecord(e0, s);
@@ -698,14 +700,18 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       }
     };
     // the update's warps per signal first (with the default correlation), then the correlation's
-    // pipeline depth and grid with the best of those
-    for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid});
+    // pipeline depth and grid with the best of those, then the update's persistent form
+    for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid, 0});
     if (tc && !failed) {
       const Shape b0 = best;
       for (int st = 4; st >= 2; --st)
-        if (st != b0.stages) trial(Shape{b0.w, st, b0.grid});
+        if (st != b0.stages) trial(Shape{b0.w, st, b0.grid, 0});
       const Shape b1 = best;
-      trial(Shape{b1.w, b1.stages, h->sm_count - h->sm_count / 8});
+      trial(Shape{b1.w, b1.stages, h->sm_count - h->sm_count / 8, 0});
+    }
+    if (!failed) {
+      const Shape b2 = best;
+      trial(Shape{b2.w, b2.stages, b2.grid, 1});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -713,22 +719,25 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       h->ws.upd_w = saved.w;
       h->ws.tc_stages = saved.stages;
       h->ws.tc_grid = saved.grid;
+      h->ws.upd_persist = saved.persist;
       return OMP_ERR_CUDA;
     }
     if (cache) {
       if (FILE* f = std::fopen(cache, "a")) {
-        std::fprintf(f, "%s|%d,%d,%d\n", key, best.w, best.stages, best.grid);
+        std::fprintf(f, "%s|%d,%d,%d,%d\n", key, best.w, best.stages, best.grid, best.persist);
         std::fclose(f);
       }
     }
   }
   if (best.w != saved.w || best.stages != saved.stages || best.grid != saved.grid ||
-      best.w != h->ws.upd_w || best.stages != h->ws.tc_stages || best.grid != h->ws.tc_grid) {
+      best.persist != saved.persist || best.w != h->ws.upd_w || best.stages != h->ws.tc_stages ||
+      best.grid != h->ws.tc_grid || best.persist != h->ws.upd_persist) {
     // captured graphs hold the old launch shapes
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
   }
   h->ws.upd_w = best.w;
+  h->ws.upd_persist = best.persist;
   if (tc) {
     h->ws.tc_stages = best.stages;
     h->ws.tc_grid = best.grid;
@@ -737,10 +746,12 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   return check_launch();
 }
 
-omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* corr_stages, int32_t* corr_ctas) {
+omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* update_persistent,
+                      int32_t* corr_stages, int32_t* corr_ctas) {
   if (!h) return OMP_ERR_INVALID_ARGUMENT;
   const bool tc = h->ws.prec != OMP_PREC_FP32;
   if (update_warps) *update_warps = h->ws.upd_w;
+  if (update_persistent) *update_persistent = h->ws.upd_persist;
   if (corr_stages) *corr_stages = tc ? h->ws.tc_stages : 0;
   if (corr_ctas) *corr_ctas = tc ? h->ws.tc_grid : 0;
   return OMP_OK;

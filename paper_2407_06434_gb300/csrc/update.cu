@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, 
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) *ws.kdev = 0;
+  if (blockIdx.x == 0 && ws.upd_ctr)
+    for (int i = threadIdx.x; i <= ws.Smax; i += blockDim.x) ws.upd_ctr[i] = 0;
   if (b >= B) return;
   const float* y = args->Y + static_cast<size_t>(b) * ws.M;
   float* r = ws.R32 + static_cast<size_t>(b) * ws.Mp;

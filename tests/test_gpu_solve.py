@@ -448,9 +448,9 @@ def test_autotune_choice_and_cache(tmp_path, monkeypatch):
     X, S_ = s.solve(Ad, Yd, w.S)                     # captures a graph with the default shape
     choice = omp.omp_autotune(s.h, Ad, Yd, w.S, 0.0, repeats=1)
     assert choice in (1, 2, 4, 8)
-    tw, tst, tg = omp.omp_tuning(s.h)
+    tw, tpe, tst, tg = omp.omp_tuning(s.h)
     _, sms = omp.omp_handle_info(s.h)
-    assert tw == choice and tst in (2, 3, 4) and tg in (sms, sms - sms // 8)
+    assert tw == choice and tpe in (0, 1) and tst in (2, 3, 4) and tg in (sms, sms - sms // 8)
     X, S_, n_iter, resid, stop = s.solve(Ad, Yd, w.S, diagnostics=True)
     torch.cuda.synchronize()
     rows = np.arange(0, w.B, 16)
@@ -458,19 +458,19 @@ def test_autotune_choice_and_cache(tmp_path, monkeypatch):
     parity.compare(A, Y[rows], ref, S_.cpu().numpy()[rows], X.cpu().numpy()[rows],
                    n_iter.cpu().numpy()[rows], resid.cpu().numpy()[rows], rows=rows)
     s.close()
-    assert cache.read_text().strip().endswith(f"|{choice},{tst},{tg}")
+    assert cache.read_text().strip().endswith(f"|{choice},{tst},{tg},{tpe}")
     s2 = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
     assert omp.omp_autotune(s2.h, Ad, Yd, w.S, 0.0, repeats=1) == choice
-    assert omp.omp_tuning(s2.h) == (tw, tst, tg)
+    assert omp.omp_tuning(s2.h) == (tw, tpe, tst, tg)
     assert len(cache.read_text().strip().splitlines()) == 1
     s2.close()
-    # every correlation shape gives the same results (cache lines force each one)
+    # every shape gives the same results (cache lines force each one)
     outs = []
-    for st, g in ((4, sms), (3, sms), (2, sms), (4, sms - sms // 8)):
-        cache.write_text(f"{_tune_key(w)}|{choice},{st},{g}\n")
+    for st, g, pe in ((4, sms, 0), (3, sms, 0), (2, sms, 0), (4, sms - sms // 8, 0), (4, sms, 1)):
+        cache.write_text(f"{_tune_key(w)}|{choice},{st},{g},{pe}\n")
         s3 = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
         omp.omp_autotune(s3.h, Ad, Yd, w.S, 0.0, repeats=1)
-        assert omp.omp_tuning(s3.h) == (choice, st, g)
+        assert omp.omp_tuning(s3.h) == (choice, pe, st, g)
         X3, S3 = s3.solve(Ad, Yd, w.S)
         outs.append((X3.cpu().numpy(), S3.cpu().numpy()))
         s3.close()

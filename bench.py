@@ -219,7 +219,7 @@ def run_gpu(args):
         X = torch.empty((w.B, w.S), dtype=torch.float32, device=dev)
         sup = torch.empty((w.B, w.S), dtype=torch.int32, device=dev)
         omp.omp_prepare_dictionary(h, Ad)
-        tuned = omp.omp_autotune(h, Ad, Yd, w.S, w.eps, repeats=2)
+        tuned = omp.omp_autotune(h, Ad, Yd, w.S, w.eps, repeats=4)
         shapes = omp.omp_tuning(h)
         for _ in range(args.warmup):
             omp.omp_solve_batch(h, Ad, Yd, w.S, w.eps, X, sup)
@@ -356,6 +356,7 @@ def run_gpu(args):
                    "update_persistent": bool(chosen["shapes"][1]),
                    "correlation_stages": chosen["shapes"][2] or None,
                    "correlation_ctas": chosen["shapes"][3] or None,
+                   "correlation_cluster": chosen["shapes"][4] or None,
                    "update_gather": "24-bit copy of A (3 bytes an element)" if args.gather24
                    else "FP32 rows",
                    "l2": "flushed between timed steps (512 MiB write)",

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(p.stdout + p.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(srcs), max(4, os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

@@ -1,0 +1,13 @@
+// The append/update kernels with eight warps per signal (the code is in append.cuh; each warp
+// count is a translation unit of its own, so the build compiles them in parallel).
+#include "append.cuh"
+
+namespace ompk {
+
+cudaError_t configure_update_w8(const Ws& ws) { return set_attr_w<8>(ws); }
+
+void launch_update_w8(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s) {
+  launch_w<8>(ws, V, k, B, S, eps, eps_rel, s);
+}
+
+}  // namespace ompk

@@ -46,7 +46,7 @@ constexpr double kDepRtol = 1e-10;    // dependent-atom test: delta <= 1e-10 ||a
 constexpr int kStopIters = 0, kStopEps = 1, kStopDependent = 2, kStopZero = 3;
 
 // Quantised paths: a signal's pruning threshold for the correlation of step `step` and the score
-// error bound (per unit of ||r||) of that step's quantised residual (see append.cu)
+// error bound (per unit of ||r||) of that step's quantised residual (see append.cuh)
 struct alignas(16) TauRec {
   float tau;
   float eps;
@@ -63,6 +63,7 @@ struct Ws {
   int tc_tn;       // atom tiles of 256
   int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
   int tc_stages;   // operand stages of the correlation's pipeline (2..4; autotuned)
+  int tc_cl;       // CTAs per cluster sharing each atom tile by multicast (1, 2, 4; autotuned)
   int upd_w;       // append/update kernel: warps per signal (1, 2, 4, 8; autotuned)
   int upd_persist; // append/update kernel: persistent grid taking positions from upd_ctr (autotuned)
   int* upd_ctr;    // Smax + 1 per-iteration position counters of the persistent form (zeroed by init)
@@ -206,20 +207,25 @@ __device__ __forceinline__ void two_sum(float& s, float& e, float x) {
 // that the loop advances.
 __device__ __forceinline__ int iter_of(const Ws& ws, int k) { return k >= 0 ? k : *ws.kdev; }
 
+
 // Persistent schedule of the tensor-core correlation (shared by the correlation kernel, which
-// writes candidate slots, and the kernels that merge them). Units u = s * Tn + t over signal
-// tiles s and atom tiles t; Geff CTAs each own a contiguous range of at least `cmin` units.
-__host__ __device__ __forceinline__ void tc_sched(int L, int G, int Tn, int cmin, int& T, int& Geff) {
+// writes candidate slots, and the kernels that merge them). The G CTAs form clusters of CL, and
+// cluster rank r works on signal tile s = CL sg + r of each group sg of CL consecutive tiles.
+// Units u = sg * Tn + t over tile groups sg and atom tiles t; Geff clusters each own a
+// contiguous range of at least `cmin` units (with CL = 1 a cluster is one CTA).
+__host__ __device__ __forceinline__ void tc_sched(int L, int G, int Tn, int cmin, int CL, int& T,
+                                                  int& Geff) {
   const int St = (L + kSigTile - 1) / kSigTile;
-  T = St * Tn;
+  T = (St + CL - 1) / CL * Tn;
   int g = T / cmin;
   if (g < 1) g = 1;
-  Geff = g < G ? g : G;
+  const int nc = G / CL;
+  Geff = g < nc ? g : nc;
 }
 __host__ __device__ __forceinline__ int tc_start(int g, int T, int Geff) {
   return static_cast<int>(static_cast<long long>(g) * T / Geff);
 }
-// the CTA whose range contains unit u
+// the cluster whose range contains unit u
 __host__ __device__ __forceinline__ int tc_owner(int u, int T, int Geff) {
   return static_cast<int>((static_cast<long long>(u + 1) * Geff - 1) / T);
 }
@@ -227,9 +233,9 @@ __host__ __device__ __forceinline__ int tc_owner(int u, int T, int Geff) {
 // piece (one per part of the atom columns of each unit)
 __device__ __forceinline__ int tc_piece_count(const Ws& ws, int L, int p) {
   int T, Geff;
-  tc_sched(L, ws.tc_grid, ws.tc_tn, ws.tc_cmin, T, Geff);
-  const int s = p / kSigTile;
-  return kTcParts * (tc_owner(s * ws.tc_tn + ws.tc_tn - 1, T, Geff) - tc_owner(s * ws.tc_tn, T, Geff) + 1);
+  tc_sched(L, ws.tc_grid, ws.tc_tn, ws.tc_cmin, ws.tc_cl, T, Geff);
+  const int sg = p / kSigTile / ws.tc_cl;
+  return kTcParts * (tc_owner(sg * ws.tc_tn + ws.tc_tn - 1, T, Geff) - tc_owner(sg * ws.tc_tn, T, Geff) + 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -259,6 +265,15 @@ void launch_set_args(CallArgs* dst, const CallArgs& v, cudaStream_t s);
 cudaError_t configure_update_kernels(const Ws& ws);
 int update_slots(int Mp, int W);
 int update_default_warps(int Mp);
+// per warp count (append_w1.cu .. append_w8.cu)
+cudaError_t configure_update_w1(const Ws& ws);
+cudaError_t configure_update_w2(const Ws& ws);
+cudaError_t configure_update_w4(const Ws& ws);
+cudaError_t configure_update_w8(const Ws& ws);
+void launch_update_w1(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
+void launch_update_w2(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
+void launch_update_w4(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
+void launch_update_w8(const Ws& ws, int V, int k, int B, int S, float eps, int eps_rel, cudaStream_t s);
 
 // learned proposal (restricted.cu, mlp.cu)
 size_t restricted_smem_per_signal(int S, int K, int Mp);
@@ -278,5 +293,6 @@ void tc_fill_sched(Ws& ws, int sm_count);
 cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan);
 void tc_destroy(TcPlan* plan);
 void launch_corr_tc(const Ws& ws, const TcPlan* plan, int k, int B, cudaStream_t s);
+int tc_fit_grid(int prec, int nst, int cl, int grid);
 
 }  // namespace ompk

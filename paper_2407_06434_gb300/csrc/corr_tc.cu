@@ -15,7 +15,7 @@
 // mainloop's minimum units per CTA (`cmin`) bounds the pieces per tile by kPieces / EPI_PARTS.
 //
 // Each row may carry a pruning threshold from the previous step's update (a lower bound on its
-// best score less three score error bounds, see append.cu): columns at or below it are not
+// best score less three score error bounds, see append.cuh): columns at or below it are not
 // inserted, which removes most of the insertion work once the solve is past its first step.
 #include "tcgemm.cuh"
 
@@ -115,7 +115,7 @@ struct EpiTop8 {
       ts[0] = __uint_as_float(lbk | 31u);
       ti[0] = lbi;
     }
-    const int piece = g - tc_owner(s * ws.tc_tn, T, Geff);
+    const int piece = g - tc_owner(s / ws.tc_cl * ws.tc_tn, T, Geff);
     const size_t off =
         (static_cast<size_t>(p) * ws.pieces + EPI_PARTS * piece + part) * kMaxTopk;
 #pragma unroll
@@ -159,8 +159,8 @@ struct EpiTop8 {
       cur_s = s;
       reset();
       thr0 = pf_tau_s == s ? pf_tau : load_tau(s);
-      pf_tau_s = s + 1;  // the next signal tile of this CTA's range, if any
-      pf_tau = load_tau(s + 1);
+      pf_tau_s = s + ws.tc_cl;  // the next signal tile of this CTA's range, if any
+      pf_tau = load_tau(s + ws.tc_cl);
     }
     const float4 v = pf_t == t ? pf : load_scales(t);
     __syncwarp();  // every lane has finished with the previous unit's scales
@@ -250,7 +250,8 @@ struct EpiTop8 {
   }
 };
 
-template <int PREC, int NST>
+// CL CTAs per cluster; tm_a's box is BN / CL atoms (each CTA loads and multicasts one slice)
+template <int PREC, int NST, int CL>
 __global__ void __launch_bounds__(THREADS, 1)
     corr_tc_kernel(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
                    const __grid_constant__ CUtensorMap tm_a, Ws ws, int k) {
@@ -262,14 +263,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   epi.L = L;
   const int row_tiles = (L + BM - 1) / BM;
   const int ktiles = ws.Mp * (PREC == OMP_PREC_BF16 ? 2 : 1) / KB;
-  gemm_body<PREC, EpiTop8<PREC>, NST>((k & 1) ? &tm_r1 : &tm_r0, &tm_a, row_tiles, ws.tc_tn, ktiles,
-                                      ws.tc_cmin, ws.err, epi);
+  gemm_body<PREC, EpiTop8<PREC>, NST, CL>((k & 1) ? &tm_r1 : &tm_r0, &tm_a, row_tiles, ws.tc_tn,
+                                          ktiles, ws.tc_cmin, ws.err, epi);
 }
 
 }  // namespace
 
 struct TcPlan {
-  CUtensorMap r0, r1, a;
+  CUtensorMap r0, r1;
+  CUtensorMap a[3];  // atoms in boxes of BN, BN / 2 and BN / 4 rows (clusters of 1, 2, 4)
   int grid;
 };
 
@@ -278,11 +280,41 @@ int tc_pieces() { return kPieces; }
 void tc_fill_sched(Ws& ws, int sm_count) {
   ws.tc_grid = sm_count;
   ws.tc_stages = STAGES;
+  ws.tc_cl = 1;
   ws.tc_tn = (ws.N + BN - 1) / BN;
   // a tile of Tn units meets at most ceil(Tn / cmin) + 1 CTA ranges of >= cmin units
   constexpr int kMaxPieces = kPieces / EPI_PARTS;
   ws.tc_cmin = (ws.tc_tn + (kMaxPieces - 2) - 1) / (kMaxPieces - 2);
 }
+
+namespace {
+template <int PREC, int NST, int CL>
+const void* kern() {
+  return reinterpret_cast<const void*>(corr_tc_kernel<PREC, NST, CL>);
+}
+// Clusters only where one CTA fills more than half an SM's shared memory: 3 or 4 stages of 48 KB
+// (clusters of 4), 4 or 6 stages of 32 KB (pairs). Two CTAs on one SM would take turns at the
+// whole of its TMEM (tcgen05.alloc waits), and two clusters, each with one CTA holding an SM's
+// TMEM and one waiting for the other's SM, would wait for each other at the cluster barrier for
+// ever.
+static_assert(2 * smem_bytes(3, 4) > 232448 && 2 * smem_bytes(4, 2) > 232448,
+              "a clustered CTA must fill more than half an SM");
+// every instantiation of one precision, by stages and cluster size: 2, 3, 4 stages of 48 KB for
+// one CTA, 4 or 6 of 32 KB for a pair (the 2-SM MMA), 3 or 4 of 48 KB for four; nullptr for any
+// other pair of values
+template <int PREC>
+const void* kern_of(int nst, int cl) {
+  if (cl == 4) return nst == 3 ? kern<PREC, 3, 4>() : nst == 4 ? kern<PREC, 4, 4>() : nullptr;
+  if (cl == 2) return nst == 4 ? kern<PREC, 4, 2>() : nst == 6 ? kern<PREC, 6, 2>() : nullptr;
+  if (cl == 1)
+    return nst == 2 ? kern<PREC, 2, 1>() : nst == 3 ? kern<PREC, 3, 1>() : nst == 4 ? kern<PREC, 4, 1>() : nullptr;
+  return nullptr;
+}
+const void* kern_of(int prec, int nst, int cl) {
+  return prec == OMP_PREC_BF16 ? kern_of<OMP_PREC_BF16>(nst, cl) : kern_of<OMP_PREC_FP8_E4M3>(nst, cl);
+}
+int cl_index(int cl) { return cl == 4 ? 2 : cl == 2 ? 1 : 0; }
+}  // namespace
 
 cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
   *plan = nullptr;
@@ -291,21 +323,19 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
   const void* a = ws.prec == OMP_PREC_BF16 ? static_cast<const void*>(ws.A16) : static_cast<const void*>(ws.A8);
   const bool ok = make_kmajor_map(&p->r0, ws.Rq[0], ws.prec, ws.Bpad, ws.Mp, BM) &&
                   make_kmajor_map(&p->r1, ws.Rq[1], ws.prec, ws.Bpad, ws.Mp, BM) &&
-                  make_kmajor_map(&p->a, a, ws.prec, ws.N, ws.Mp, BN);
+                  make_kmajor_map(&p->a[0], a, ws.prec, ws.N, ws.Mp, BN) &&
+                  make_kmajor_map(&p->a[1], a, ws.prec, ws.N, ws.Mp, BN / 2) &&
+                  make_kmajor_map(&p->a[2], a, ws.prec, ws.N, ws.Mp, BN / 4);
   if (!ok) {
     delete p;
     return cudaErrorNotSupported;
   }
   cudaError_t e = cudaSuccess;
-  auto attr = [&](const void* kern, int nst) {
-    if (e == cudaSuccess) e = set_smem_attr(kern, smem_bytes(nst));
-  };
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 4>), 4);
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 3>), 3);
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_BF16, 2>), 2);
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 4>), 4);
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 3>), 3);
-  attr(reinterpret_cast<const void*>(corr_tc_kernel<OMP_PREC_FP8_E4M3, 2>), 2);
+  for (int prec : {static_cast<int>(OMP_PREC_BF16), static_cast<int>(OMP_PREC_FP8_E4M3)})
+    for (int nst : {2, 3, 4, 6})
+      for (int cl = 1; cl <= 4; cl <<= 1)
+        if (e == cudaSuccess && kern_of(prec, nst, cl))
+          e = set_smem_attr(kern_of(prec, nst, cl), smem_bytes(nst, cl));
   if (e != cudaSuccess) {
     delete p;
     return e;
@@ -316,24 +346,55 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
 
 void tc_destroy(TcPlan* plan) { delete plan; }
 
-template <int PREC>
-void launch_prec(const Ws& ws, const TcPlan* plan, int k, cudaStream_t s) {
-  // the persistent grid is the workspace's (the candidate slots are laid out for it)
-  const int grid = ws.tc_grid;
-  if (ws.tc_stages == 3)
-    corr_tc_kernel<PREC, 3><<<grid, THREADS, smem_bytes(3), s>>>(plan->r0, plan->r1, plan->a, ws, k);
-  else if (ws.tc_stages == 2)
-    corr_tc_kernel<PREC, 2><<<grid, THREADS, smem_bytes(2), s>>>(plan->r0, plan->r1, plan->a, ws, k);
-  else
-    corr_tc_kernel<PREC, 4><<<grid, THREADS, smem_bytes(4), s>>>(plan->r0, plan->r1, plan->a, ws, k);
+// The grid for clusters of `cl` CTAs: at most `grid` CTAs, a multiple of cl, no more clusters
+// than fit on the device at once (0 if none fit, or if there is no such kernel).
+int tc_fit_grid(int prec, int nst, int cl, int grid) {
+  const int want = grid / cl;
+  if (!kern_of(prec, nst, cl)) return 0;
+  if (cl == 1 || want < 1) return want * cl;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(want * cl));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem_bytes(nst, cl);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern_of(prec, nst, cl), &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (n < want ? n : want) * cl;
 }
 
 void launch_corr_tc(const Ws& ws, const TcPlan* plan, int k, int B, cudaStream_t s) {
   (void)B;
-  if (ws.prec == OMP_PREC_BF16)
-    launch_prec<OMP_PREC_BF16>(ws, plan, k, s);
-  else
-    launch_prec<OMP_PREC_FP8_E4M3>(ws, plan, k, s);
+  // the persistent grid is the workspace's (the candidate slots are laid out for it), a
+  // multiple of the cluster size
+  const int cl = ws.tc_cl;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(ws.tc_grid));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem_bytes(ws.tc_stages, cl);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = cl > 1 ? 1 : 0;
+  const CUtensorMap* r0 = &plan->r0;
+  const CUtensorMap* r1 = &plan->r1;
+  const CUtensorMap* am = &plan->a[cl_index(cl)];
+  void* args[] = {const_cast<CUtensorMap*>(r0), const_cast<CUtensorMap*>(r1), const_cast<CUtensorMap*>(am),
+                  const_cast<Ws*>(&ws), &k};
+  const void* kernel = kern_of(ws.prec, ws.tc_stages, cl);
+  if (kernel && ws.tc_grid % cl == 0) cudaLaunchKernelExC(&cfg, kernel, args);  // else: no shape
 }
 
 }  // namespace ompk

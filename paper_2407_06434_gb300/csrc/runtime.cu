@@ -387,6 +387,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   ws.Fstride = (static_cast<int64_t>(ws.Smax) * (ws.Smax + 1) / 2 + 3) / 4 * 4;
   ws.upd_w = update_default_warps(ws.Mp);
   ws.pieces = d.precision == OMP_PREC_FP32 ? 0 : tc_pieces();
+  ws.tc_cl = 1;
   if (d.precision != OMP_PREC_FP32) tc_fill_sched(ws, h->sm_count);
   const size_t N = ws.N, Mp = ws.Mp, Bm = ws.Bmax, Bp = ws.Bpad, Sm = ws.Smax;
   const size_t qbytes = d.precision == OMP_PREC_BF16 ? 2 : 1;
@@ -642,25 +643,34 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   std::snprintf(key, sizeof(key), "%.64s M=%d N=%d prec=%d B=%lld S=%d", prop.name, h->ws.M, h->ws.N,
                 h->ws.prec, static_cast<long long>(B), S);
   const bool tc = h->ws.prec != OMP_PREC_FP32;
-  // a launch shape: update warps per signal, correlation stages and persistent CTAs
+  // a launch shape: update warps per signal, correlation stages, persistent CTAs (asked for;
+  // the launch takes the largest multiple of the cluster size that fits), update persistent
+  // form, correlation cluster size
   struct Shape {
-    int w, stages, grid, persist;
+    int w, stages, grid, persist, cl;
+  };
+  auto fitted = [&](const Shape& c) {
+    return tc ? tc_fit_grid(h->ws.prec, c.stages, c.cl, c.grid) : c.grid;
   };
   auto valid = [&](const Shape& c) {
-    return update_slots(h->ws.Mp, c.w) != 0 &&
-           (!tc || (c.stages >= 2 && c.stages <= 4 && c.grid >= 1 && c.grid <= h->sm_count));
+    return update_slots(h->ws.Mp, c.w) != 0 && (c.persist == 0 || c.persist == 1) &&
+           (!tc || (c.stages >= 2 && c.stages <= 6 && c.grid >= 1 && c.grid <= h->sm_count &&
+                    (c.cl == 1 || c.cl == 2 || c.cl == 4) && fitted(c) >= c.cl));
   };
-  const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid, h->ws.upd_persist};
-  Shape best{0, saved.stages, saved.grid, saved.persist};
-  if (cache) {  // a previous run's choice: "key|w", "key|w,stages,grid" or "key|w,stages,grid,persist"
+  const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid, h->ws.upd_persist, h->ws.tc_cl};
+  Shape best{0, saved.stages, saved.grid, saved.persist, saved.cl};
+  if (cache) {  // a previous run's choice: "key|w", "key|w,stages,grid", "key|w,stages,grid,persist"
+                // or "key|w,stages,grid,persist,cluster"
     if (FILE* f = std::fopen(cache, "r")) {
       char line[512];
       while (std::fgets(line, sizeof(line), f)) {
         char* bar = std::strrchr(line, '|');
         Shape c = saved;
-        const int n = bar ? std::sscanf(bar + 1, "%d,%d,%d,%d", &c.w, &c.stages, &c.grid, &c.persist) : 0;
+        const int n = bar ? std::sscanf(bar + 1, "%d,%d,%d,%d,%d", &c.w, &c.stages, &c.grid, &c.persist,
+                                        &c.cl)
+                          : 0;
         if (std::strncmp(line, key, std::strlen(key)) == 0 && line[std::strlen(key)] == '|' &&
-            (n == 1 || n == 3 || n == 4) && valid(c) && (c.persist == 0 || c.persist == 1))
+            (n == 1 || n == 3 || n == 4 || n == 5) && valid(c))
           best = c;
       }
       std::fclose(f);
@@ -674,45 +684,115 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
     a.Y = Y;
     a.X = h->x_stage;
     a.support = h->s_stage;
+    launch_set_args(h->args_dev, a, s);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OMP_ERR_CUDA;
-    float best_ms = 0.f;
     bool failed = false;
-    auto trial = [&](const Shape& c) {
-      if (failed || !valid(c)) return;
+    const int b = static_cast<int>(B);
+    auto apply = [&](const Shape& c) {
       h->ws.upd_w = c.w;
       h->ws.tc_stages = c.stages;
-      h->ws.tc_grid = c.grid;
+      h->ws.tc_grid = fitted(c);
       h->ws.upd_persist = c.persist;
-      launch_set_args(h->args_dev, a, s);
-      enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);  // warm-up
+      h->ws.tc_cl = c.cl;
+    };
+    // One shape's solve as a solve runs it: a graph replay when the handle uses graphs (its
+    // kernels' arguments are fixed at capture), else direct launches.
+    struct Run {
+      Shape c;
+      cudaGraphExec_t exec;
+    };
+    auto make_run = [&](const Shape& c, Run* r) {
+      apply(c);
+      r->c = c;
+      r->exec = nullptr;
+      if (!h->d.use_graph) return true;
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        enqueue_solve(h, solve_ws(h, false), b, S, eps, false, h->cap_stream);
+        ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && g != nullptr;
+      }
+      if (ok) ok = cudaGraphInstantiate(&r->exec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      if (!ok) cudaGetLastError();
+      return ok;
+    };
+    auto launch_run = [&](const Run& r) {
+      if (r.exec) {
+        if (cudaGraphLaunch(r.exec, s) != cudaSuccess) failed = true;
+      } else {
+        apply(r.c);
+        enqueue_solve(h, solve_ws(h, false), b, S, eps, false, s);
+      }
+    };
+    auto time_run = [&](const Run& r) {
       cudaEventRecord(e0, s);
-      for (int r = 0; r < repeats; ++r) enqueue_solve(h, h->ws, static_cast<int>(B), S, eps, false, s);
+      launch_run(r);
       cudaEventRecord(e1, s);
       float ms = 0.f;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        failed = true;
+      return ms;
+    };
+    Run inc{};
+    auto drop = [](Run& r) {
+      if (r.exec) cudaGraphExecDestroy(r.exec);
+      r.exec = nullptr;
+    };
+    // The first valid shape (the default) is the incumbent. A challenger is timed alternately
+    // with it, `repeats` solves each after one warm-up of each, so that clock ramp and drift fall
+    // on both alike, and replaces it only when clearly faster (3% less time), so that noise does
+    // not move a solve off a good shape.
+    auto trial = [&](const Shape& c) {
+      if (failed || !valid(c)) return;
+      if (!best.w) {
+        if (!make_run(c, &inc)) {
+          failed = true;
+          return;
+        }
+        best = c;
+        for (int r = 0; r < 2 && !failed; ++r) time_run(inc);  // warm-up of the GPU and the shape
+        return;
+      }
+      Run ch{};
+      if (!make_run(c, &ch)) {
         failed = true;
         return;
       }
-      if (!best.w || ms < best_ms) {
+      time_run(ch);  // warm-up
+      float t_inc = 0.f, t_ch = 0.f;
+      for (int r = 0; r < repeats && !failed; ++r) {
+        t_inc += time_run(inc);
+        t_ch += time_run(ch);
+      }
+      if (!failed && t_ch < 0.97f * t_inc) {
+        drop(inc);
+        inc = ch;
         best = c;
-        best_ms = ms;
+      } else {
+        drop(ch);
       }
     };
     // the update's warps per signal first (with the default correlation), then the correlation's
-    // pipeline depth and grid with the best of those, then the update's persistent form
-    for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid, 0});
+    // cluster size, pipeline depth and grid with the best of those, then the update's
+    // persistent form
+    for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid, 0, saved.cl});
     if (tc && !failed) {
       const Shape b0 = best;
-      for (int st = 4; st >= 2; --st)
-        if (st != b0.stages) trial(Shape{b0.w, st, b0.grid, 0});
+      for (int cl = 1; cl <= 4; cl <<= 1)
+        if (cl != b0.cl) trial(Shape{b0.w, b0.stages, b0.grid, 0, cl});
       const Shape b1 = best;
-      trial(Shape{b1.w, b1.stages, h->sm_count - h->sm_count / 8, 0});
+      for (int st : {4, 3, 2, 6})
+        if (st != b1.stages) trial(Shape{b1.w, st, b1.grid, 0, b1.cl});
+      const Shape b2 = best;
+      trial(Shape{b2.w, b2.stages, h->sm_count - h->sm_count / 8, 0, b2.cl});
     }
     if (!failed) {
-      const Shape b2 = best;
-      trial(Shape{b2.w, b2.stages, b2.grid, 1});
+      const Shape b3 = best;
+      trial(Shape{b3.w, b3.stages, b3.grid, 1, b3.cl});
     }
+    drop(inc);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (failed) {
@@ -720,18 +800,21 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       h->ws.tc_stages = saved.stages;
       h->ws.tc_grid = saved.grid;
       h->ws.upd_persist = saved.persist;
+      h->ws.tc_cl = saved.cl;
       return OMP_ERR_CUDA;
     }
     if (cache) {
       if (FILE* f = std::fopen(cache, "a")) {
-        std::fprintf(f, "%s|%d,%d,%d,%d\n", key, best.w, best.stages, best.grid, best.persist);
+        std::fprintf(f, "%s|%d,%d,%d,%d,%d\n", key, best.w, best.stages, best.grid, best.persist, best.cl);
         std::fclose(f);
       }
     }
   }
-  if (best.w != saved.w || best.stages != saved.stages || best.grid != saved.grid ||
-      best.persist != saved.persist || best.w != h->ws.upd_w || best.stages != h->ws.tc_stages ||
-      best.grid != h->ws.tc_grid || best.persist != h->ws.upd_persist) {
+  const int best_grid = fitted(best);
+  if (best.w != saved.w || best.stages != saved.stages || best_grid != saved.grid ||
+      best.persist != saved.persist || best.cl != saved.cl || best.w != h->ws.upd_w ||
+      best.stages != h->ws.tc_stages || best_grid != h->ws.tc_grid ||
+      best.persist != h->ws.upd_persist || best.cl != h->ws.tc_cl) {
     // captured graphs hold the old launch shapes
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
@@ -740,20 +823,22 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   h->ws.upd_persist = best.persist;
   if (tc) {
     h->ws.tc_stages = best.stages;
-    h->ws.tc_grid = best.grid;
+    h->ws.tc_grid = best_grid;
+    h->ws.tc_cl = best.cl;
   }
   if (choice_out) *choice_out = best.w;
   return check_launch();
 }
 
 omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* update_persistent,
-                      int32_t* corr_stages, int32_t* corr_ctas) {
+                      int32_t* corr_stages, int32_t* corr_ctas, int32_t* corr_cluster) {
   if (!h) return OMP_ERR_INVALID_ARGUMENT;
   const bool tc = h->ws.prec != OMP_PREC_FP32;
   if (update_warps) *update_warps = h->ws.upd_w;
   if (update_persistent) *update_persistent = h->ws.upd_persist;
   if (corr_stages) *corr_stages = tc ? h->ws.tc_stages : 0;
   if (corr_ctas) *corr_ctas = tc ? h->ws.tc_grid : 0;
+  if (corr_cluster) *corr_cluster = tc ? h->ws.tc_cl : 0;
   return OMP_OK;
 }
 

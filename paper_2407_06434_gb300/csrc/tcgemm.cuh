@@ -7,10 +7,16 @@
 // K in 128-byte stages (64 BF16 or 128 E4M3 elements, 4 MMAs of 32 bytes each per stage).
 // Schedule: units u = s * Tn + t over row tiles s and column tiles t; CTA g of Geff owns the
 // contiguous range [floor(g T / Geff), floor((g + 1) T / Geff)), Geff = min(grid, T / cmin).
+// Clusters (template CL = 2 or 4, the correlation's choice): the CL CTAs of a cluster run the
+// same column tiles in lockstep on CL consecutive row tiles (units then run over row-tile groups,
+// g and Geff count clusters), and each loads 1/CL of every B_op stage with a TMA multicast to all
+// of them, so the L2 sends each B_op tile once per cluster instead of once per CTA; a stage is
+// refilled once the MMAs of every CTA have released it (its empty barrier counts CL commits).
 //
 // Roles (64 + 128 EPI_PARTS threads, one CTA per SM):
-//   warp 0 lane 0  TMA producer, NST stages (4 by default; 2 to 4 for the correlation, the
-//                  autotuner's choice) of 16 KB (A_op) + 32 KB (B_op)
+//   warp 0 lane 0  TMA producer, NST stages (4 by default; for the correlation 2, 3, 4 or 9,
+//                  the autotuner's choice) of 16 KB (A_op) + 32 KB (B_op), or with 9 stages
+//                  of 8 KB + 16 KB (K rows of 64 bytes)
 //   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
 //   warps 2..      epilogue, EPI_PARTS warps per TMEM lane quarter (a warp may only read the
 //                  quarter warp % 4), each over EPI_COLS of the unit's 256 columns: tcgen05.ld
@@ -52,10 +58,14 @@ static_assert(THREADS >= EPI_PARTS * BM, "the peer slots are initialised one per
 static_assert(EPI_COLS % 32 == 0, "epilogue chunks are 32 columns");
 constexpr int TMEM_COLS = 2 * BN;
 constexpr int EPI_SCRATCH = EPI_COLS;  // shared floats per epilogue warp
+// Bytes of an operand stage: the A_op tile and the B_op tile, or for a CTA pair (cl = 2, the
+// 2-SM MMA) the A_op tile and half the B_op tile.
+__host__ __device__ constexpr int stage_bytes(int cl) { return BM * KB + (cl == 2 ? BN / 2 : BN) * KB; }
 // dynamic shared memory of a mainloop with `nst` operand stages
-__host__ __device__ constexpr int smem_bytes(int nst) {
-  return nst * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_SCRATCH * 4 + EPI_PARTS * BM * 8;
+__host__ __device__ constexpr int smem_bytes(int nst, int cl = 1) {
+  return nst * stage_bytes(cl) + 1024 + 256 + EPI_WARPS * EPI_SCRATCH * 4 + EPI_PARTS * BM * 8;
 }
+static_assert(smem_bytes(6, 2) <= 232448, "6 pair stages fit in a CTA's shared memory");
 constexpr int SMEM_BYTES = smem_bytes(STAGES);
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
@@ -109,6 +119,46 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// The same copy delivered to every CTA of the cluster in `mask`, at the same shared offsets,
+// each completing on its own mbarrier at offset `bar`.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders the mbarrier initialisations before any
+// peer's copy or arrival
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// arrive on the mbarrier at shared offset `bar` of cluster CTA `rank`
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(bar), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -124,36 +174,88 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          (static_cast<uint64_t>(2) << 61);
 }
 
-// Instruction descriptor: FP32 accumulator, A/B K-major, N = 256, M = 128;
-// A/B format BF16 (kind::f16) or E4M3 (kind::f8f6f4).
-template <int PREC>
+// Instruction descriptor: FP32 accumulator, A/B K-major, N = 256, M = 128 (one CTA) or 256 (a CTA
+// pair, PAIR); A/B format BF16 (kind::f16) or E4M3 (kind::f8f6f4).
+template <int PREC, bool PAIR = false>
 __host__ __device__ constexpr uint32_t idesc() {
   return (1u << 4) | ((PREC == OMP_PREC_BF16 ? 1u : 0u) << 7) |
          ((PREC == OMP_PREC_BF16 ? 1u : 0u) << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
-         (static_cast<uint32_t>(BM >> 4) << 24);
+         (static_cast<uint32_t>((PAIR ? 2 * BM : BM) >> 4) << 24);
 }
 
-template <int PREC>
+// One MMA. With PAIR (issued by the pair's even CTA only) it spans both CTAs: rows 0..127 of
+// A_op and of D in this CTA, rows 128..255 in the peer, and half of B_op's rows in each, all at
+// the same shared and tensor-memory offsets.
+template <int PREC, bool PAIR = false>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  if (PREC == OMP_PREC_BF16) {
+  if (PREC == OMP_PREC_BF16 && !PAIR) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc<PREC>()), "r"(accumulate)
+        "l"(a), "l"(b), "r"(idesc<PREC, PAIR>()), "r"(accumulate)
+        : "memory");
+  } else if (!PAIR) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<PREC, PAIR>()), "r"(accumulate)
+        : "memory");
+  } else if (PREC == OMP_PREC_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<PREC, PAIR>()), "r"(accumulate)
         : "memory");
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc<PREC>()), "r"(accumulate)
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<PREC, PAIR>()), "r"(accumulate)
         : "memory");
   }
 }
 
+// Arrive on the mbarrier at offset `bar` once this thread's MMAs have completed: of this CTA, or
+// with `mask` of every cluster CTA in it. PAIR: the commit of pair MMAs (every tcgen05 operation
+// of a pair kernel is cta_group::2).
+template <bool PAIR = false>
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
+  if (PAIR)
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+template <bool PAIR = false>
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  if (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
+}
+
+// A copy into this CTA's shared memory that completes on an mbarrier of either CTA of the pair
+// (`bar_cl` a shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar_cl) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cl)
       : "memory");
+}
+// the shared::cluster address of offset `a` in cluster CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  return ra;
 }
 
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32]) {
@@ -206,45 +308,66 @@ __device__ __forceinline__ void top8_insert(float (&s)[8], int (&ix)[8], float v
 
 
 // ------------------------------------------------------------------------------- mainloop
-template <int PREC, class Epi, int NST = STAGES>
+// CL = 1: one CTA per unit. CL = 2: a CTA pair on two SMs runs one 256 x 256 MMA per K step
+// (tcgen05 cta_group::2, issued by the even CTA): each CTA holds its own 128 A_op rows and half
+// of the B_op tile, so an SM takes in 32 KB per stage instead of 48 KB; the peer's copies
+// complete on the even CTA's full barriers, the even CTA's commits reach both CTAs' empty and
+// accumulator barriers, and both CTAs' epilogues release the accumulator to the even CTA.
+// CL = 4: four CTAs each run their own MMA and load a quarter of every B_op tile, multicast to
+// all four.
+template <int PREC, class Epi, int NST = STAGES, int CL = 1>
 __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtensorMap* tm_b,
                                           int row_tiles, int col_tiles, int ktiles, int cmin,
                                           unsigned int* err, Epi& epi) {
+  static_assert(CL == 1 || CL == 2 || CL == 4, "clusters of 1, 2 or 4 CTAs");
+  constexpr bool PAIR = CL == 2;
+  constexpr bool MCAST = CL == 4;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int T = row_tiles * col_tiles;
+  // with CL > 1 the launch is in clusters of CL consecutive CTAs; rank r takes signal tile
+  // CL sg + r of each unit's tile group sg and loads rows [r BN / CL, (r + 1) BN / CL) of the
+  // unit's B_op tile
+  const int rank = CL > 1 ? static_cast<int>(cluster_rank()) : 0;
+  const bool lead = rank == 0;  // PAIR: the CTA that issues the MMAs
+  const int T = (row_tiles + CL - 1) / CL * col_tiles;
   if (T <= 0) return;
   int Geff = T / (cmin > 0 ? cmin : 1);
   if (Geff < 1) Geff = 1;
-  if (Geff > static_cast<int>(gridDim.x)) Geff = gridDim.x;
-  const int g = blockIdx.x;
-  if (g >= Geff) return;  // uniform across the CTA
+  if (Geff > static_cast<int>(gridDim.x) / CL) Geff = gridDim.x / CL;
+  const int g = blockIdx.x / CL;
+  if (g >= Geff) return;  // uniform across the cluster
+  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const int Tn = col_tiles;
+  constexpr int SA = A_BYTES;              // this CTA's A_op tile
+  constexpr int SB = stage_bytes(CL) - SA; // the B_op bytes in this CTA's stage
+  constexpr int SS = stage_bytes(CL);
   const int u0 = static_cast<int>(static_cast<long long>(g) * T / Geff);
   const int u1 = static_cast<int>(static_cast<long long>(g + 1) * T / Geff);
 
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t bars = base + NST * STAGE_BYTES;
+  const uint32_t bars = base + NST * SS;
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (NST + s); };
   auto tfull = [&](int a) { return bars + 8u * (2 * NST + a); };
   auto tempty = [&](int a) { return bars + 8u * (2 * NST + 2 + a); };
   const uint32_t drain = bars + 8u * (2 * NST + 4);
+  const uint32_t done = bars + 8u * (2 * NST + 5);  // the cluster's CTAs have finished
   uint8_t* bars_gen = smem_raw + (bars - raw);
-  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * NST + 5));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * NST + 5) + 4);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * NST + 6));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * NST + 6) + 4);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+      mbar_init(empty(s), MCAST ? CL : 1);  // multicast: every CTA's MMAs read the stage's slices
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull(a), 1);
-      mbar_init(tempty(a), EPI_WARPS);
+      mbar_init(tempty(a), PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // PAIR: both CTAs' epilogues
     }
     mbar_init(drain, 1);
+    mbar_init(done, CL);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -253,14 +376,24 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
       reinterpret_cast<unsigned long long*>(bars_gen + 256 + EPI_WARPS * EPI_SCRATCH * 4);
   if (threadIdx.x < EPI_PARTS * BM) peers[threadIdx.x] = 0xffffffff00000000ull;  // tag -1
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(const_cast<uint32_t*>(tmem_slot))),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // PAIR: one warp of each CTA of the pair allocates, together
+    if (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(const_cast<uint32_t*>(tmem_slot))),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(const_cast<uint32_t*>(tmem_slot))),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // no copy or arrival reaches a peer's barriers before their init
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int kelems = KB / (PREC == OMP_PREC_BF16 ? 2 : 1);  // K elements per stage
@@ -274,16 +407,31 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     for (int s = 0; s < NST; ++s) last_ph[s] = -1;
     bool ok = true;
     for (int u = u0; u < u1 && ok; ++u) {
-      const int s = u / Tn, t = u - s * Tn;
+      const int sg = u / Tn, t = u - sg * Tn;
+      const int s = sg * CL + rank;
       for (int kc = 0; kc < ktiles; ++kc) {
         if (!mbar_wait(empty(stage), ph ^ 1u, abort_flag, err)) {
           ok = false;
           break;
         }
-        const uint32_t dst = base + stage * STAGE_BYTES;
-        mbar_expect_tx(full(stage), STAGE_BYTES);
-        tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
-        tma_load_2d(dst + A_BYTES, tm_b, kc * kelems, t * BN, full(stage));
+        const uint32_t dst = base + stage * SS;
+        if (PAIR) {
+          // both CTAs' copies of the stage complete on the even CTA's full barrier, which
+          // expects the bytes of both
+          if (lead) mbar_expect_tx(full(stage), 2 * SS);
+          const uint32_t fb = cluster_addr(full(stage), 0);
+          tma_load_2d_pair(dst, tm_a, kc * kelems, s * BM, fb);
+          tma_load_2d_pair(dst + SA, tm_b, kc * kelems, t * BN + rank * (BN / 2), fb);
+        } else {
+          // the stage's bytes: this CTA's A_op tile and the CL slices of the B_op tile
+          mbar_expect_tx(full(stage), SS);
+          tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
+          if (MCAST)
+            tma_load_2d_mc(dst + SA + rank * (SB / CL), tm_b, kc * kelems, t * BN + rank * (BN / CL),
+                           full(stage), kMask);
+          else
+            tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(stage));
+        }
 #pragma unroll
         for (int q = 0; q < NST; ++q)  // static indices keep last_ph in registers
           if (q == stage) last_ph[q] = static_cast<int>(ph);
@@ -293,13 +441,14 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         }
       }
     }
-    if (!ok) {
-      // let every copy this thread issued land before the CTA exits
+    if (!ok && (!PAIR || lead)) {
+      // let every copy this thread issued land before the CTA exits (a pair's odd CTA cannot
+      // see its copies complete: they signal the even CTA, which drains them with its own)
       volatile int no_abort = 0;
       for (int s = 0; s < NST; ++s)
         if (last_ph[s] >= 0) mbar_wait(full(s), static_cast<uint32_t>(last_ph[s]), &no_abort, err);
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == 1 && lane == 0 && (!PAIR || lead)) {
     // ------------------------------------------------------------------ MMA issuer
     int stage = 0;
     uint32_t ph = 0;
@@ -319,24 +468,30 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
           break;
         }
         tc_fence_after();
-        const uint32_t a_addr = base + stage * STAGE_BYTES;
-        const uint32_t b_addr = a_addr + A_BYTES;
+        const uint32_t a_addr = base + stage * SS;
+        const uint32_t b_addr = a_addr + SA;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma<PREC>(d, sdesc(a_addr + kk * 32), sdesc(b_addr + kk * 32), (kc | kk) != 0);
-        mma_commit(empty(stage));
+          mma<PREC, PAIR>(d, sdesc(a_addr + kk * 32), sdesc(b_addr + kk * 32), (kc | kk) != 0);
+        if (CL == 1)
+          mma_commit<false>(empty(stage));
+        else
+          mma_commit_mc<PAIR>(empty(stage), kMask);  // every CTA may refill its part of it
         if (++stage == NST) {
           stage = 0;
           ph ^= 1u;
         }
       }
       if (!ok) break;
-      mma_commit(tfull(acc));
+      if (PAIR)
+        mma_commit_mc<true>(tfull(acc), kMask);  // both CTAs' accumulators are ready
+      else
+        mma_commit<false>(tfull(acc));
       acc ^= 1;
       if (acc == 0) aph ^= 1u;
     }
     // wait until every MMA this thread issued has completed
-    mma_commit(drain);
+    mma_commit<PAIR>(drain);
     volatile int no_abort = 0;
     mbar_wait(drain, 0, &no_abort, err);
   } else if (warp >= 2) {
@@ -351,7 +506,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     uint32_t aph = 0;
     bool ok = true;
     for (int u = u0; u < u1; ++u) {
-      const int s = u / Tn, t = u - s * Tn;
+      const int sg = u / Tn, t = u - sg * Tn;
+      const int s = sg * CL + rank;
       epi.unit(s, t);
       if (!mbar_wait(tfull(acc), aph, abort_flag, err)) {
         ok = false;
@@ -361,7 +517,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
       const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) +
                              static_cast<uint32_t>(acc * BN + part * EPI_COLS);
       // one 32-column load at a time; once the last load has landed the accumulator goes back
-      // to the MMA before that chunk is scanned
+      // to the MMA (PAIR: to the even CTA's barrier) before that chunk is scanned
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         uint32_t cur[32];
@@ -370,7 +526,12 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
         if (c + 1 == CH) {
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(tempty(acc));
+          if (lane == 0) {
+            if (PAIR && !lead)
+              mbar_arrive_remote(tempty(acc), 0);
+            else
+              mbar_arrive(tempty(acc));
+          }
         }
         epi.chunk(s, t, part * EPI_COLS + c * 32, cur);
       }
@@ -381,11 +542,32 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) {
+    // A peer's copies into this CTA's stages, its MMAs' arrivals on this CTA's barriers and (a
+    // pair) its MMAs into this CTA's tensor memory must not outlive the CTA: each CTA, its MMAs
+    // drained, tells every CTA of the cluster, and goes on once all have told it (bounded: a
+    // peer that timed out arrives within its own limits)
+    if (threadIdx.x == 0) {
+      for (int r = 0; r < CL; ++r) mbar_arrive_remote(done, static_cast<uint32_t>(r));
+      const long long t0 = clock64();
+      while (!mbar_try_cluster(done, 0)) {
+        if (clock64() - t0 > 4 * kWaitCycles) {
+          atomicOr(err, OMP_DEVERR_WAIT_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncthreads();
+  }
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
-                 : "memory");
+    if (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                   : "memory");
   }
 }
 

@@ -1,6 +1,6 @@
 // Per-signal kernels around the OMP iteration: initialisation, live-set compaction, the final
 // back-substitution x = F b (FP64), and the top-k output of omp_correlate_topk. The per-iteration
-// append and residual update is in append.cu.
+// append and residual update is in append.cuh.
 #include <mutex>
 
 #include "common.cuh"

@@ -119,7 +119,7 @@ def load(path: Optional[str] = None):
         "omp_solve_batch_learned": (_I32, [_P, _P, _P, _P, _I64, _I32, _F32, _P, _P, _P, _P, _P, _P]),
         "omp_autotune": (_I32, [_P, _P, _P, _I64, _I32, _F32, _I32, ctypes.POINTER(_I32), _P]),
         "omp_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
-                              ctypes.POINTER(_I32)]),
+                              ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -328,11 +328,12 @@ def omp_autotune(h: Handle, A, Y, S: int, eps: float = 0.0, repeats: int = 2, st
 
 
 def omp_tuning(h: Handle):
-    """(update warps per signal, update persistent form, correlation stages, correlation CTAs)."""
-    w, pe, st, g = _I32(0), _I32(0), _I32(0), _I32(0)
-    _check(load().omp_tuning(h.ptr, ctypes.byref(w), ctypes.byref(pe), ctypes.byref(st), ctypes.byref(g)),
-           "omp_tuning")
-    return w.value, pe.value, st.value, g.value
+    """(update warps per signal, update persistent form, correlation stages, correlation CTAs,
+    correlation CTAs per cluster)."""
+    w, pe, st, g, cl = _I32(0), _I32(0), _I32(0), _I32(0), _I32(0)
+    _check(load().omp_tuning(h.ptr, ctypes.byref(w), ctypes.byref(pe), ctypes.byref(st), ctypes.byref(g),
+                             ctypes.byref(cl)), "omp_tuning")
+    return w.value, pe.value, st.value, g.value, cl.value
 
 
 def omp_handle_info(h: Handle):

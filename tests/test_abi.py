@@ -44,8 +44,8 @@ def test_status_strings(lib):
 
 def test_desc_default(lib):
     d = omp.omp_desc_default(1024, 8192)
-    assert (d.M, d.N, d.max_iters, d.precision, d.rescore_topk, d.eps_relative, d.use_graph) == \
-        (1024, 8192, 64, 1, 8, 1, 1)
+    assert (d.M, d.N, d.max_iters, d.precision, d.rescore_topk, d.eps_relative, d.use_graph,
+            d.gather24) == (1024, 8192, 64, 1, 8, 1, 1, 0)
 
 
 def test_invalid_arguments_rejected_before_device_work(lib):
@@ -54,7 +54,8 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     d = omp.omp_desc()
     lib.omp_desc_default(ctypes.byref(d), 64, 256)
     for field, bad in [("M", 0), ("N", 1), ("max_batch", 0), ("max_iters", 0),
-                       ("max_iters", 300), ("precision", 7), ("rescore_topk", 9)]:
+                       ("max_iters", 300), ("precision", 7), ("rescore_topk", 9),
+                       ("gather24", 2)]:
         dd = omp.omp_desc.from_buffer_copy(d)
         setattr(dd, field, bad)
         assert lib.omp_create(ctypes.byref(dd), ctypes.byref(h)) == 1, field

@@ -448,9 +448,10 @@ def test_autotune_choice_and_cache(tmp_path, monkeypatch):
     X, S_ = s.solve(Ad, Yd, w.S)                     # captures a graph with the default shape
     choice = omp.omp_autotune(s.h, Ad, Yd, w.S, 0.0, repeats=1)
     assert choice in (1, 2, 4, 8)
-    tw, tpe, tst, tg = omp.omp_tuning(s.h)
+    tw, tpe, tst, tg, tcl = omp.omp_tuning(s.h)
     _, sms = omp.omp_handle_info(s.h)
-    assert tw == choice and tpe in (0, 1) and tst in (2, 3, 4) and tg in (sms, sms - sms // 8)
+    assert tw == choice and tpe in (0, 1) and tst in (2, 3, 4, 6) and tcl in (1, 2, 4)
+    assert 1 <= tg <= sms and tg % tcl == 0
     X, S_, n_iter, resid, stop = s.solve(Ad, Yd, w.S, diagnostics=True)
     torch.cuda.synchronize()
     rows = np.arange(0, w.B, 16)
@@ -458,25 +459,71 @@ def test_autotune_choice_and_cache(tmp_path, monkeypatch):
     parity.compare(A, Y[rows], ref, S_.cpu().numpy()[rows], X.cpu().numpy()[rows],
                    n_iter.cpu().numpy()[rows], resid.cpu().numpy()[rows], rows=rows)
     s.close()
-    assert cache.read_text().strip().endswith(f"|{choice},{tst},{tg},{tpe}")
+    # the cache records the CTAs asked for; the launch takes a multiple of the cluster size
+    cw, cst, cg, cpe, ccl = (int(v) for v in cache.read_text().strip().split("|")[-1].split(","))
+    assert (cw, cst, cpe, ccl) == (choice, tst, tpe, tcl) and tg <= cg <= sms
     s2 = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
     assert omp.omp_autotune(s2.h, Ad, Yd, w.S, 0.0, repeats=1) == choice
-    assert omp.omp_tuning(s2.h) == (tw, tpe, tst, tg)
+    assert omp.omp_tuning(s2.h) == (tw, tpe, tst, tg, tcl)
     assert len(cache.read_text().strip().splitlines()) == 1
     s2.close()
     # every shape gives the same results (cache lines force each one)
     outs = []
-    for st, g, pe in ((4, sms, 0), (3, sms, 0), (2, sms, 0), (4, sms - sms // 8, 0), (4, sms, 1)):
-        cache.write_text(f"{_tune_key(w)}|{choice},{st},{g},{pe}\n")
+    for st, g, pe, cl in ((4, sms, 0, 1), (3, sms, 0, 1), (2, sms, 0, 1), (4, sms - sms // 8, 0, 1),
+                          (4, sms, 1, 1), (4, sms, 0, 2), (6, sms - sms // 8, 0, 2), (4, sms, 0, 4),
+                          (3, sms, 0, 4)):
+        cache.write_text(f"{_tune_key(w)}|{choice},{st},{g},{pe},{cl}\n")
         s3 = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision="bf16")
         omp.omp_autotune(s3.h, Ad, Yd, w.S, 0.0, repeats=1)
-        assert omp.omp_tuning(s3.h) == (choice, pe, st, g)
+        t3 = omp.omp_tuning(s3.h)
+        assert t3[:3] == (choice, pe, st) and t3[4] == cl
+        assert (t3[3] == g) if cl == 1 else (0 < t3[3] <= g and t3[3] % cl == 0)
         X3, S3 = s3.solve(Ad, Yd, w.S)
         outs.append((X3.cpu().numpy(), S3.cpu().numpy()))
         s3.close()
     for X3, S3 in outs[1:]:
         assert np.array_equal(S3, outs[0][1])
         assert np.array_equal(X3.view(np.uint32), outs[0][0].view(np.uint32))
+
+
+@pytest.mark.parametrize("prec,pcode", [("bf16", 1), ("fp8", 2)])
+def test_cluster_multicast_ragged(tmp_path, monkeypatch, prec, pcode):
+    """Correlation CTA pairs (one 256-row MMA across two SMs, each holding half of the atom
+    tile) and clusters of 4 CTAs (each loads a quarter of the atom tile and multicasts it): on a
+    batch of 700 signals (6 signal tiles, the last ragged, so the last cluster of 4 has two tiles
+    past the batch) with a residual stop that retires signals (the live count, and with it the
+    tile count, shrinks from step to step), every shape gives results bit-identical to one CTA
+    per tile, and the results match the oracle."""
+    from paper_2407_06434_gb300 import omp
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("OMP_AUTOTUNE_CACHE", str(cache))
+    w = gen.get_config("gaussian_64x256_s8_b16", M=512, N=2304, B=700, S=24, s_min=4, s_max=24,
+                       sigma=1e-3, col_scale=1.0)
+    A = gen.dictionary(w, seed=21)
+    Y, *_ = gen.signals(w, A, seed=21)
+    Ad, Yd = dev_dict(A), torch.from_numpy(Y).cuda()
+    eps = 1e-2  # signals stop after 4 to 24 steps
+    outs = []
+    for st, cl in ((4, 1), (4, 2), (6, 2), (4, 4), (3, 4)):
+        s = omp.OmpSolver(w.M, w.N, max_batch=w.B, max_iters=w.S, precision=prec)
+        sms = omp.omp_handle_info(s.h)[1]
+        cache.write_text(f"{_tune_key(w, pcode)}|1,{st},{sms},0,{cl}\n")
+        omp.omp_autotune(s.h, Ad, Yd, w.S, eps, repeats=1)
+        assert omp.omp_tuning(s.h)[2] == st and omp.omp_tuning(s.h)[4] == cl
+        X, S_, n_iter, resid, _ = s.solve(Ad, Yd, w.S, eps, diagnostics=True)
+        torch.cuda.synchronize()
+        outs.append((X.cpu().numpy(), S_.cpu().numpy(), n_iter.cpu().numpy(), resid.cpu().numpy()))
+        s.close()
+    n_it = outs[0][2]
+    assert n_it.min() < w.S and n_it.max() > n_it.min()  # signals retire at different steps
+    for X, S_, it, r in outs[1:]:
+        assert np.array_equal(S_, outs[0][1]) and np.array_equal(it, n_it)
+        assert np.array_equal(X.view(np.uint32), outs[0][0].view(np.uint32))
+        assert np.array_equal(r.view(np.uint32), outs[0][3].view(np.uint32))
+    rows = np.arange(0, w.B, 7)
+    X, S_, it, r = outs[2]
+    ref = oracle.omp_batch(A, Y[rows], w.S, eps=eps)
+    parity.compare(A, Y[rows], ref, S_[rows], X[rows], it[rows], r[rows], eps=eps, rows=rows)
 
 
 def test_read_bandwidth_probe():

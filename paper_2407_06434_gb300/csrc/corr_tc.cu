@@ -214,32 +214,46 @@ struct EpiTop8 {
       if (static_cast<int>(v >> 32) == cur_s && othr > 0.f)
         thr = fmaxf(thr, __uint_as_float(__float_as_uint(othr) - 1u));
     }
-    uint32_t mask = 0, kmax = 0;
+    // The chunk's scores, as bits, and their largest: scores are non-negative, so they order as
+    // their bits do (a NaN's bits above every number's). One multiply and one integer max per
+    // column; the per-column threshold test and the best-column search below run only for a lane
+    // whose largest score beats its threshold or its list's best key (few, once lists are warm).
+    uint32_t sv[32];
+    uint32_t mbits = 0;
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
       const float4 sc = sc4[j4];
-      const float v[4] = {fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x,
-                          fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y,
-                          fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z,
-                          fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w};
+      sv[4 * j4 + 0] = __float_as_uint(fabsf(__uint_as_float(cur[4 * j4 + 0])) * sc.x);
+      sv[4 * j4 + 1] = __float_as_uint(fabsf(__uint_as_float(cur[4 * j4 + 1])) * sc.y);
+      sv[4 * j4 + 2] = __float_as_uint(fabsf(__uint_as_float(cur[4 * j4 + 2])) * sc.z);
+      sv[4 * j4 + 3] = __float_as_uint(fabsf(__uint_as_float(cur[4 * j4 + 3])) * sc.w);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 4 * j4 + q;
-        mask |= (v[q] > thr ? 1u : 0u) << j;
-        // columns past N score 0 (zero escale), so they never beat a real column's key
-        if (kTrack) kmax = max(kmax, (__float_as_uint(v[q]) & ~31u) | static_cast<uint32_t>(31 - j));
-      }
+      for (int q = 0; q < 4; ++q) mbits = max(mbits, sv[4 * j4 + q]);
     }
-    if (kTrack && (kmax & ~31u) > (lbk & ~31u)) {  // strictly higher: an earlier column keeps a tie
-      lbk = kmax;
-      lbi = nb + 31 - static_cast<int>(kmax & 31u);
+    // the list's best column as a key: score bits with the low 5 replaced by 31 - the column's
+    // place, so that among scores equal above those bits the lowest column wins; columns past N
+    // score 0 (zero escale), so they never beat a real column's key
+    if (kTrack && (mbits & ~31u) > (lbk & ~31u)) {  // strictly higher: an earlier column keeps a tie
+      int jb = 31;
+#pragma unroll
+      for (int j = 31; j >= 0; --j)
+        if ((sv[j] & ~31u) == (mbits & ~31u)) jb = j;
+      lbk = (mbits & ~31u) | static_cast<uint32_t>(31 - jb);
+      lbi = nb + jb;
     }
-    if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
-    mask &= ~seeded;
+    // x > thr for x, thr >= 0 exactly when bits(x) > bits(thr); a negative thr (an unfilled list
+    // with no pruning threshold) passes every column
+    uint32_t mask = 0;
+    if (thr < 0.f || mbits > __float_as_uint(thr)) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) mask |= (__uint_as_float(sv[j]) > thr ? 1u : 0u) << j;
+      if (lim < 32) mask &= lim > 0 ? (0xffffffffu >> (32 - lim)) : 0u;
+      mask &= ~seeded;
+    }
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      const float score = fabsf(__uint_as_float(pick32(cur, j))) * scl[j];
+      const float score = __uint_as_float(pick32(sv, j));
       if (score > ts[7]) top8_insert(ts, ti, score, nb + j);
     }
     *reinterpret_cast<volatile unsigned long long*>(peers + part * BM + row) =

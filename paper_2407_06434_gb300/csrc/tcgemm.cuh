@@ -273,6 +273,19 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// The same wait, with the loaded registers as its operands, so that no read of them is
+// scheduled before it
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                 "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+                 "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]),
+                 "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+                 "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]),
+                 "+r"(v[31])
+               :
+               : "memory");
+}
 
 // v[j] for a run-time j without local memory: a 5-level select tree
 __device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], int j) {
@@ -516,13 +529,14 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
       tc_fence_after();
       const uint32_t taddr = tmem + (static_cast<uint32_t>(lg * 32) << 16) +
                              static_cast<uint32_t>(acc * BN + part * EPI_COLS);
-      // one 32-column load at a time; once the last load has landed the accumulator goes back
+      // one 32-column load at a time (the wait takes the loaded registers as operands, so no
+      // read of them moves above it); once the last load has landed the accumulator goes back
       // to the MMA (PAIR: to the even CTA's barrier) before that chunk is scanned
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         uint32_t cur[32];
         tmem_ld32_issue(taddr + c * 32, cur);
-        tmem_ld_wait();
+        tmem_ld_wait(cur);
         if (c + 1 == CH) {
           tc_fence_before();
           __syncwarp();

@@ -199,11 +199,10 @@ omp_status omp_solve_batch_trace(omp_handle h, const float* A, const float* Y, i
 /* Autotuner (the batching change's launch shapes, Sec. 3.5's batched solve): times solves of
  * (A, Y, B, S, eps) for each valid launch shape and keeps the fastest on the handle: first the
  * append/update kernel's warps per signal (1, 2, 4 or 8 for the padded signal length), then, on
- * the tensor-core paths, the correlation's cluster size (1; 2, a CTA pair running 256-row MMAs
- * across two SMs, each SM holding half of the atom tile; 4, four CTAs sharing each atom tile by
- * multicast), its pipeline depth (2, 3 or 4 operand stages of 48 KB; a pair 4 or 6 of 32 KB;
- * four CTAs 3 or 4) and its persistent grid (every SM, or seven eighths of them; with clusters, the
- * largest multiple of the cluster size that fits at once), then the update kernel's persistent form (a grid of the blocks that fit on
+ * the tensor-core paths, the correlation's CTAs per tile (1; or 2, a CTA pair running 256-row
+ * MMAs across two SMs, each SM holding half of the atom tile), its pipeline depth (2, 3 or 4
+ * operand stages of 48 KB; a pair 4 or 6 of 32 KB) and its persistent grid (every SM, or seven
+ * eighths of them; a pair launch takes the largest even count whose pairs fit at once), then the update kernel's persistent form (a grid of the blocks that fit on
  * the GPU taking positions from a counter) against one block per signal. Each solve runs as a
  * solve does (a graph replay when the handle uses graphs); a challenger is timed alternately
  * with the incumbent, `repeats` solves each, and replaces it only when at least 3% faster, the
@@ -217,8 +216,8 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
                         int32_t repeats, int32_t* choice_out, void* stream);
 
 /* The handle's current launch shapes (each pointer may be NULL): update warps per signal, update
- * persistent form (0 or 1), correlation operand stages, persistent CTAs and CTAs per cluster (the
- * last three 0 on the FP32 path). Host only. */
+ * persistent form (0 or 1), correlation operand stages, persistent CTAs and CTAs per cluster (1,
+ * or 2 for the 2-SM MMA pair; the last three 0 on the FP32 path). Host only. */
 omp_status omp_tuning(omp_handle h, int32_t* update_warps, int32_t* update_persistent,
                       int32_t* corr_stages, int32_t* corr_ctas, int32_t* corr_cluster);
 

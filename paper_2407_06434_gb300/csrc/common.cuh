@@ -62,8 +62,8 @@ struct Ws {
   int tc_grid;     // tensor-core correlation: persistent grid size
   int tc_tn;       // atom tiles of 256
   int tc_cmin;     // minimum work units per CTA (bounds the pieces per signal tile)
-  int tc_stages;   // operand stages of the correlation's pipeline (2..4; autotuned)
-  int tc_cl;       // CTAs per cluster sharing each atom tile by multicast (1, 2, 4; autotuned)
+  int tc_stages;   // operand stages of the correlation's pipeline (2..4; a pair 4 or 6; autotuned)
+  int tc_cl;       // CTAs per correlation tile: 1, or 2 for the 2-SM MMA pair (autotuned)
   int upd_w;       // append/update kernel: warps per signal (1, 2, 4, 8; autotuned)
   int upd_persist; // append/update kernel: persistent grid taking positions from upd_ctr (autotuned)
   int* upd_ctr;    // Smax + 1 per-iteration position counters of the persistent form (zeroed by init)

@@ -264,7 +264,8 @@ struct EpiTop8 {
   }
 };
 
-// CL CTAs per cluster; tm_a's box is BN / CL atoms (each CTA loads and multicasts one slice)
+// CL CTAs per cluster (1, or a pair running the 2-SM MMA); tm_a's box is BN / CL atoms (each CTA
+// of a pair loads half of the atom tile)
 template <int PREC, int NST, int CL>
 __global__ void __launch_bounds__(THREADS, 1)
     corr_tc_kernel(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 struct TcPlan {
   CUtensorMap r0, r1;
-  CUtensorMap a[3];  // atoms in boxes of BN, BN / 2 and BN / 4 rows (clusters of 1, 2, 4)
+  CUtensorMap a[2];  // atoms in boxes of BN rows (one CTA) and BN / 2 rows (a pair)
   int grid;
 };
 
@@ -306,19 +307,15 @@ template <int PREC, int NST, int CL>
 const void* kern() {
   return reinterpret_cast<const void*>(corr_tc_kernel<PREC, NST, CL>);
 }
-// Clusters only where one CTA fills more than half an SM's shared memory: 3 or 4 stages of 48 KB
-// (clusters of 4), 4 or 6 stages of 32 KB (pairs). Two CTAs on one SM would take turns at the
-// whole of its TMEM (tcgen05.alloc waits), and two clusters, each with one CTA holding an SM's
-// TMEM and one waiting for the other's SM, would wait for each other at the cluster barrier for
-// ever.
-static_assert(2 * smem_bytes(3, 4) > 232448 && 2 * smem_bytes(4, 2) > 232448,
-              "a clustered CTA must fill more than half an SM");
+// Pairs only where one CTA fills more than half an SM's shared memory (4 or 6 stages of 32 KB).
+// Two CTAs on one SM would take turns at the whole of its TMEM (tcgen05.alloc waits), and two
+// pairs, each with one CTA holding an SM's TMEM and one waiting for the other's SM, would wait
+// for each other at the cluster barrier for ever.
+static_assert(2 * smem_bytes(4, 2) > 232448, "a paired CTA must fill more than half an SM");
 // every instantiation of one precision, by stages and cluster size: 2, 3, 4 stages of 48 KB for
-// one CTA, 4 or 6 of 32 KB for a pair (the 2-SM MMA), 3 or 4 of 48 KB for four; nullptr for any
-// other pair of values
+// one CTA, 4 or 6 of 32 KB for a pair (the 2-SM MMA); nullptr for any other pair of values
 template <int PREC>
 const void* kern_of(int nst, int cl) {
-  if (cl == 4) return nst == 3 ? kern<PREC, 3, 4>() : nst == 4 ? kern<PREC, 4, 4>() : nullptr;
   if (cl == 2) return nst == 4 ? kern<PREC, 4, 2>() : nst == 6 ? kern<PREC, 6, 2>() : nullptr;
   if (cl == 1)
     return nst == 2 ? kern<PREC, 2, 1>() : nst == 3 ? kern<PREC, 3, 1>() : nst == 4 ? kern<PREC, 4, 1>() : nullptr;
@@ -327,7 +324,7 @@ const void* kern_of(int nst, int cl) {
 const void* kern_of(int prec, int nst, int cl) {
   return prec == OMP_PREC_BF16 ? kern_of<OMP_PREC_BF16>(nst, cl) : kern_of<OMP_PREC_FP8_E4M3>(nst, cl);
 }
-int cl_index(int cl) { return cl == 4 ? 2 : cl == 2 ? 1 : 0; }
+int cl_index(int cl) { return cl == 2 ? 1 : 0; }
 }  // namespace
 
 cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
@@ -338,8 +335,7 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
   const bool ok = make_kmajor_map(&p->r0, ws.Rq[0], ws.prec, ws.Bpad, ws.Mp, BM) &&
                   make_kmajor_map(&p->r1, ws.Rq[1], ws.prec, ws.Bpad, ws.Mp, BM) &&
                   make_kmajor_map(&p->a[0], a, ws.prec, ws.N, ws.Mp, BN) &&
-                  make_kmajor_map(&p->a[1], a, ws.prec, ws.N, ws.Mp, BN / 2) &&
-                  make_kmajor_map(&p->a[2], a, ws.prec, ws.N, ws.Mp, BN / 4);
+                  make_kmajor_map(&p->a[1], a, ws.prec, ws.N, ws.Mp, BN / 2);
   if (!ok) {
     delete p;
     return cudaErrorNotSupported;
@@ -347,7 +343,7 @@ cudaError_t tc_setup(const Ws& ws, int sm_count, TcPlan** plan) {
   cudaError_t e = cudaSuccess;
   for (int prec : {static_cast<int>(OMP_PREC_BF16), static_cast<int>(OMP_PREC_FP8_E4M3)})
     for (int nst : {2, 3, 4, 6})
-      for (int cl = 1; cl <= 4; cl <<= 1)
+      for (int cl = 1; cl <= 2; ++cl)
         if (e == cudaSuccess && kern_of(prec, nst, cl))
           e = set_smem_attr(kern_of(prec, nst, cl), smem_bytes(nst, cl));
   if (e != cudaSuccess) {

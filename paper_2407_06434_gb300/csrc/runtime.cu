@@ -644,8 +644,8 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
                 h->ws.prec, static_cast<long long>(B), S);
   const bool tc = h->ws.prec != OMP_PREC_FP32;
   // a launch shape: update warps per signal, correlation stages, persistent CTAs (asked for;
-  // the launch takes the largest multiple of the cluster size that fits), update persistent
-  // form, correlation cluster size
+  // a pair launch takes the largest even number whose pairs fit at once), update persistent
+  // form, correlation CTAs per cluster (1, or 2 for the 2-SM MMA pair)
   struct Shape {
     int w, stages, grid, persist, cl;
   };
@@ -655,7 +655,7 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
   auto valid = [&](const Shape& c) {
     return update_slots(h->ws.Mp, c.w) != 0 && (c.persist == 0 || c.persist == 1) &&
            (!tc || (c.stages >= 2 && c.stages <= 6 && c.grid >= 1 && c.grid <= h->sm_count &&
-                    (c.cl == 1 || c.cl == 2 || c.cl == 4) && fitted(c) >= c.cl));
+                    (c.cl == 1 || c.cl == 2) && fitted(c) >= c.cl));
   };
   const Shape saved{h->ws.upd_w, h->ws.tc_stages, h->ws.tc_grid, h->ws.upd_persist, h->ws.tc_cl};
   Shape best{0, saved.stages, saved.grid, saved.persist, saved.cl};
@@ -775,12 +775,12 @@ omp_status omp_autotune(omp_handle h, const float* A, const float* Y, int64_t B,
       }
     };
     // the update's warps per signal first (with the default correlation), then the correlation's
-    // cluster size, pipeline depth and grid with the best of those, then the update's
-    // persistent form
+    // CTAs per tile (one, or a pair), pipeline depth and grid with the best of those, then the
+    // update's persistent form
     for (int w = 1; w <= 8; w <<= 1) trial(Shape{w, saved.stages, saved.grid, 0, saved.cl});
     if (tc && !failed) {
       const Shape b0 = best;
-      for (int cl = 1; cl <= 4; cl <<= 1)
+      for (int cl = 1; cl <= 2; ++cl)
         if (cl != b0.cl) trial(Shape{b0.w, b0.stages, b0.grid, 0, cl});
       const Shape b1 = best;
       for (int st : {4, 3, 2, 6})

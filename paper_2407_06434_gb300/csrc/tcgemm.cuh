@@ -7,16 +7,14 @@
 // K in 128-byte stages (64 BF16 or 128 E4M3 elements, 4 MMAs of 32 bytes each per stage).
 // Schedule: units u = s * Tn + t over row tiles s and column tiles t; CTA g of Geff owns the
 // contiguous range [floor(g T / Geff), floor((g + 1) T / Geff)), Geff = min(grid, T / cmin).
-// Clusters (template CL = 2 or 4, the correlation's choice): the CL CTAs of a cluster run the
-// same column tiles in lockstep on CL consecutive row tiles (units then run over row-tile groups,
-// g and Geff count clusters), and each loads 1/CL of every B_op stage with a TMA multicast to all
-// of them, so the L2 sends each B_op tile once per cluster instead of once per CTA; a stage is
-// refilled once the MMAs of every CTA have released it (its empty barrier counts CL commits).
+// CTA pairs (template CL = 2, the correlation's choice): the two CTAs of a cluster run the same
+// column tiles in lockstep on two consecutive row tiles (units then run over row-tile pairs, g
+// and Geff count pairs), as one 256-row MMA across the two SMs (see the mainloop).
 //
 // Roles (64 + 128 EPI_PARTS threads, one CTA per SM):
-//   warp 0 lane 0  TMA producer, NST stages (4 by default; for the correlation 2, 3, 4 or 9,
-//                  the autotuner's choice) of 16 KB (A_op) + 32 KB (B_op), or with 9 stages
-//                  of 8 KB + 16 KB (K rows of 64 bytes)
+//   warp 0 lane 0  TMA producer, NST stages (4 by default; for the correlation 2, 3 or 4, the
+//                  autotuner's choice) of 16 KB (A_op) + 32 KB (B_op), or for a CTA pair 4 or 6
+//                  stages of 16 KB + 16 KB
 //   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
 //   warps 2..      epilogue, EPI_PARTS warps per TMEM lane quarter (a warp may only read the
 //                  quarter warp % 4), each over EPI_COLS of the unit's 256 columns: tcgen05.ld
@@ -119,17 +117,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// The same copy delivered to every CTA of the cluster in `mask`, at the same shared offsets,
-// each completing on its own mbarrier at offset `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -227,18 +214,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
-template <bool PAIR = false>
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  if (PAIR)
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(mask)
-        : "memory");
-  else
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(mask)
-        : "memory");
+// The pair's commit: one arrival on the mbarrier at offset `bar` of each CTA of the pair (this
+// one, and the peer through its shared::cluster address), once this thread's MMAs have completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint32_t peer_bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(peer_bar)
+               : "memory");
 }
 
 // A copy into this CTA's shared memory that completes on an mbarrier of either CTA of the pair
@@ -326,20 +308,17 @@ __device__ __forceinline__ void top8_insert(float (&s)[8], int (&ix)[8], float v
 // of the B_op tile, so an SM takes in 32 KB per stage instead of 48 KB; the peer's copies
 // complete on the even CTA's full barriers, the even CTA's commits reach both CTAs' empty and
 // accumulator barriers, and both CTAs' epilogues release the accumulator to the even CTA.
-// CL = 4: four CTAs each run their own MMA and load a quarter of every B_op tile, multicast to
-// all four.
 template <int PREC, class Epi, int NST = STAGES, int CL = 1>
 __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtensorMap* tm_b,
                                           int row_tiles, int col_tiles, int ktiles, int cmin,
                                           unsigned int* err, Epi& epi) {
-  static_assert(CL == 1 || CL == 2 || CL == 4, "clusters of 1, 2 or 4 CTAs");
+  static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
   constexpr bool PAIR = CL == 2;
-  constexpr bool MCAST = CL == 4;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // with CL > 1 the launch is in clusters of CL consecutive CTAs; rank r takes signal tile
-  // CL sg + r of each unit's tile group sg and loads rows [r BN / CL, (r + 1) BN / CL) of the
-  // unit's B_op tile
+  // with CL = 2 the launch is in clusters of two consecutive CTAs; rank r takes signal tile
+  // 2 sg + r of each unit's tile pair sg and loads rows [r BN / 2, (r + 1) BN / 2) of the unit's
+  // B_op tile
   const int rank = CL > 1 ? static_cast<int>(cluster_rank()) : 0;
   const bool lead = rank == 0;  // PAIR: the CTA that issues the MMAs
   const int T = (row_tiles + CL - 1) / CL * col_tiles;
@@ -349,10 +328,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   if (Geff > static_cast<int>(gridDim.x) / CL) Geff = gridDim.x / CL;
   const int g = blockIdx.x / CL;
   if (g >= Geff) return;  // uniform across the cluster
-  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const int Tn = col_tiles;
-  constexpr int SA = A_BYTES;              // this CTA's A_op tile
-  constexpr int SB = stage_bytes(CL) - SA; // the B_op bytes in this CTA's stage
+  constexpr int SA = A_BYTES;              // this CTA's A_op tile, then its B_op rows
   constexpr int SS = stage_bytes(CL);
   const int u0 = static_cast<int>(static_cast<long long>(g) * T / Geff);
   const int u1 = static_cast<int>(static_cast<long long>(g + 1) * T / Geff);
@@ -373,7 +350,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), MCAST ? CL : 1);  // multicast: every CTA's MMAs read the stage's slices
+      mbar_init(empty(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull(a), 1);
@@ -436,14 +413,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
           tma_load_2d_pair(dst, tm_a, kc * kelems, s * BM, fb);
           tma_load_2d_pair(dst + SA, tm_b, kc * kelems, t * BN + rank * (BN / 2), fb);
         } else {
-          // the stage's bytes: this CTA's A_op tile and the CL slices of the B_op tile
           mbar_expect_tx(full(stage), SS);
           tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
-          if (MCAST)
-            tma_load_2d_mc(dst + SA + rank * (SB / CL), tm_b, kc * kelems, t * BN + rank * (BN / CL),
-                           full(stage), kMask);
-          else
-            tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(stage));
+          tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(stage));
         }
 #pragma unroll
         for (int q = 0; q < NST; ++q)  // static indices keep last_ph in registers
@@ -486,10 +458,10 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           mma<PREC, PAIR>(d, sdesc(a_addr + kk * 32), sdesc(b_addr + kk * 32), (kc | kk) != 0);
-        if (CL == 1)
-          mma_commit<false>(empty(stage));
+        if (PAIR)
+          mma_commit_pair(empty(stage), cluster_addr(empty(stage), 1));  // both may refill it
         else
-          mma_commit_mc<PAIR>(empty(stage), kMask);  // every CTA may refill its part of it
+          mma_commit<false>(empty(stage));
         if (++stage == NST) {
           stage = 0;
           ph ^= 1u;
@@ -497,7 +469,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
       }
       if (!ok) break;
       if (PAIR)
-        mma_commit_mc<true>(tfull(acc), kMask);  // both CTAs' accumulators are ready
+        mma_commit_pair(tfull(acc), cluster_addr(tfull(acc), 1));  // both accumulators are ready
       else
         mma_commit<false>(tfull(acc));
       acc ^= 1;
@@ -557,10 +529,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   tc_fence_before();
   __syncthreads();
   if (CL > 1) {
-    // A peer's copies into this CTA's stages, its MMAs' arrivals on this CTA's barriers and (a
-    // pair) its MMAs into this CTA's tensor memory must not outlive the CTA: each CTA, its MMAs
-    // drained, tells every CTA of the cluster, and goes on once all have told it (bounded: a
-    // peer that timed out arrives within its own limits)
+    // The even CTA's MMAs into the odd CTA's tensor memory and their arrivals on its barriers
+    // must not outlive either CTA: each CTA, its MMAs drained, tells both, and goes on once both
+    // have told it (bounded: a peer that timed out arrives within its own limits)
     if (threadIdx.x == 0) {
       for (int r = 0; r < CL; ++r) mbar_arrive_remote(done, static_cast<uint32_t>(r));
       const long long t0 = clock64();

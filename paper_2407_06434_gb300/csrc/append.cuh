@@ -59,7 +59,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
                    static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
                "l"(src)
@@ -67,6 +67,8 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// wait until at most one of this thread's committed groups is still in flight
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 
 struct GroupSmem {
@@ -272,8 +274,10 @@ __device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int 
   const bool top1 = ws.prec == OMP_PREC_FP32;
   const int lane = threadIdx.x & 31;
   const int grp = 0, wig = threadIdx.x >> 5;
+  // the signal at this position and its own iteration (signals may join the loop late), from two
+  // arrays the compaction wrote side by side, so both arrive in one round trip
   const int id = ws.live[k & 1][p];
-  const int kk = ws.niter[id];  // the signal's own iteration (signals may join the loop late)
+  const int kk = ws.livek[k & 1][p];
   GroupSmem gs = group_smem(smem, grp, ws);
 
   // The candidate lists head the critical path (merge, rescoring, append), so their loads are
@@ -293,22 +297,22 @@ __device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int 
     }
   }
 
-  // Loads that do not depend on the selection go out next: the packed FP32 factor (staged in
-  // shared memory with 16-byte loads, so the serial z and F z loops wait on no global load), the
-  // support, and the norms used at the end.
+  // Loads that do not depend on the selection go out next. The packed FP32 factor (so that the
+  // serial z and F z loops wait on no global load) and the support are copied into shared memory
+  // by cp.async, which holds no register and does not stall the warp: they land while the merge
+  // and the rescoring run, and the append waits for them (the first group this warp commits).
   float* Ff = ws.F32 + static_cast<size_t>(id) * ws.Fstride;
   const bool staged = ws.Smax <= kTriMax;
   if (wig == 0) {
     if (staged) {
       const int tn4 = (kk * (kk + 1) / 2 + 3) >> 2;  // within the padded stride
-      const float4* src = reinterpret_cast<const float4*>(Ff);
-      float4* dst = reinterpret_cast<float4*>(gs.tri);
-#pragma unroll 4
-      for (int e = lane; e < tn4; e += 32) dst[e] = src[e];
+      for (int e = lane; e < tn4; e += 32) cp_async16(gs.tri + 4 * e, Ff + 4 * e);
     }
     const int* supg = ws.sup + static_cast<size_t>(id) * ws.Smax;
-    for (int i = lane; i < kk; i += 32) gs.sup[i] = supg[i];
+    for (int i = lane; i < kk; i += 32) cp_async4(gs.sup + i, supg + i);
+    cp_async_commit();
   }
+  bool rows_group = false;  // a second cp.async group (the threshold's candidate rows) follows
   const float rprev = ws.rnorm[id];
   const float ynorm = ws.ynorm[id];
   // the pruning threshold the correlation used for this position (0: none; in the units of the
@@ -427,6 +431,7 @@ __device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int 
         if (wig == 0 && lane == c) cp_async4(gs.rinv + c, ws.inv_norm + n);
       }
       cp_async_commit();
+      rows_group = true;
     }
     // FP32 rescoring: every warp dots its residual slice with each candidate's FP32 row, two
     // candidates per pass so their row loads are in flight together. With the bound, a pass
@@ -506,6 +511,7 @@ __device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int 
     ns = gs.scal[0];
   }
   if (ns < 0 || ns >= ws.N) {
+    cp_async_wait_all();  // no copy outlives the block
     if (wig == 0 && lane == 0) {
       atomicOr(ws.err, OMP_DEVERR_BAD_STATE);
       ws.flag[p] = 0;
@@ -519,7 +525,13 @@ __device__ __forceinline__ void update_position(const Ws& ws, int k, int L, int 
   // stored factor (used by the back-substitution) are FP64.
   double* Fg = ws.F + static_cast<size_t>(id) * ws.Fstride;
   if (wig == 0) {
-    __syncwarp();  // the support and the staged factor are visible to the whole warp
+    // the staged factor and the support have landed (the candidate rows of the threshold,
+    // committed after them, may still be in flight) and are visible to the whole warp
+    if (rows_group)
+      cp_async_wait_one();
+    else
+      cp_async_wait_all();
+    __syncwarp();
     const float* grow = ws.gram + static_cast<size_t>(ns) * ws.N;
     for (int i = lane; i < kk; i += 32) gs.w[i] = __ldg(grow + gs.sup[i]);
     __syncwarp();

@@ -18,6 +18,8 @@
 //     ynorm, rnorm (float), niter, stop (int)
 //   per live position p (the compacted order of the signals still iterating):
 //     live[2][Bmax]  position -> signal id, ping-pong by iteration parity
+//     livek[2][Bmax] position -> the signal's own iteration count (its niter when the list was
+//                    written), beside live, so the update reads both in one round trip
 //     cnt[Smax+2]    cnt[j+1] = live count after compaction j (cnt[0] = B)
 //     flag[Bmax]     1 if the signal at position p continues after this iteration
 //     Rq[2]          Bpad x Mp quantised residual rows in position order (tensor-core operand)
@@ -85,6 +87,7 @@ struct Ws {
   void* Rq[2];
   float* sr[2];
   int* live[2];
+  int* livek[2];   // per position: the signal's iteration count when the list was written
   int* cnt;
   int* kdev;       // iteration counter of the graph's device-side loop
   float rescore_eps;  // bound on |quantised score - FP32 score| per unit of ||r|| (0: none)

@@ -419,6 +419,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
     ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) &&
          (ws.prec != OMP_PREC_FP8_E4M3 || dalloc(h, &ws.ea, 1));
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
+  ok = ok && dalloc(h, &ws.livek[0], Bm) && dalloc(h, &ws.livek[1], Bm);
   ok = ok && dalloc(h, &ws.cnt, Sm + 2) && dalloc(h, &ws.kdev, 1) && dalloc(h, &ws.flag, Bm) && dalloc(h, &ws.cand1, Bm);
   ok = ok && dalloc(h, &ws.upd_ctr, Sm + 1);
   ok = ok && dalloc(h, &ws.F, Bm * static_cast<size_t>(ws.Fstride)) &&

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) init_kernel(Ws ws, const CallArgs* args, 
     ws.flag[b] = alive ? 1 : 0;
     ws.fb[b] = -1;
     ws.live[1][b] = b;
+    ws.livek[1][b] = 0;
     if (ws.tau) ws.tau[b] = TauRec{0.f, 0.f, -1, 0};
     if (!finite) atomicOr(ws.err, OMP_DEVERR_NONFINITE);
     if (b == 0) ws.cnt[0] = B;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(256) load_rows_kernel(Ws ws, const float* __re
   if (lane == 0) {
     ws.flag[b] = 1;
     ws.live[1][b] = b;
+    ws.livek[1][b] = 0;
     if (b == 0) ws.cnt[0] = B;
   }
 }
@@ -89,7 +91,8 @@ void launch_load_rows(const Ws& ws, const float* R, int B, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ compaction
 // Compaction step j: keeps the positions of list live[(j+1)&1] (count cnt[j]) whose flag is
-// set, in order, into live[j&1]; writes cnt[j+1]. Each block owns kCompactChunk positions and
+// set, in order, into live[j&1] (and each kept signal's iteration count into livek[j&1]); writes
+// cnt[j+1]. Each block owns kCompactChunk positions and
 // counts the kept flags before its range itself (16 flags per load), so the compaction is
 // stable and needs no inter-block communication. Kept signals get their candidate key cleared
 // and, on the tensor-core paths, their residual row quantised into position order (Rq[j&1],
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     const bool fp8_tau = tau > 0.f && ws.prec == OMP_PREC_FP8_E4M3;
     if (lane == 0) {
       out[dest] = id;
+      ws.livek[j & 1][dest] = ws.niter[id];
       ws.cand1[dest] = 0ull;
       if (ws.cand2) ws.cand2[dest] = 0ull;
       if (ws.tau_pos && !fp8_tau) ws.tau_pos[dest] = tau;

@@ -95,6 +95,8 @@ struct Ws {
   float gam_tc, gam_32;  // accumulation bounds over Mp terms: tensor core and FP32 rescoring
   TauRec* tau;     // quantised paths with the bound: per signal, next step's threshold and bound
   float* tau_pos;  // the same per live position of the current step (0: no pruning); or null
+  float* win_pos;  // per live position: three score error bounds at the row's residual (the
+                   // window below the row's running best outside which columns are pruned)
   uint8_t* flag;
   unsigned long long* cand1;
   float* cand_s;

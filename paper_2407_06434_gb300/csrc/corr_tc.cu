@@ -96,6 +96,8 @@ struct EpiTop8 {
   float thr0;    // this row's pruning threshold in the current signal tile (-1: none)
   float pf_tau;  // the row's threshold in signal tile pf_tau_s, loaded ahead
   int pf_tau_s;
+  float win0;    // this row's window below its running best (0: none)
+  float pf_win;  // the row's window in signal tile pf_tau_s, loaded ahead
 
   __device__ void reset() {
 #pragma unroll
@@ -133,6 +135,17 @@ struct EpiTop8 {
     const float v = __ldg(ws.tau_pos + p);
     return v > 0.f ? v : -1.f;
   }
+  // Three score error bounds at the row's residual (written per live position by the
+  // compaction, in the units of the scores): a column whose score is that far below the best
+  // score the row has shown so far has an FP32 score more than two bounds below the best FP32
+  // score, so it can be neither the pick nor a rescoring candidate that changes it. This prunes
+  // where no previous step left a threshold (the first step) as well as past the best column.
+  __device__ float load_win(int s) const {
+    const int p = s * BM + row;
+    if (!ws.win_pos || p >= L) return 0.f;
+    const float v = __ldg(ws.win_pos + p);
+    return v > 0.f ? v : 0.f;
+  }
   // this lane's EPI_COLS / 32 consecutive scales of the warp's columns of tile t
   __device__ float4 load_scales(int t) const {
     static_assert(EPI_COLS == 128, "one float4 per lane");
@@ -151,6 +164,7 @@ struct EpiTop8 {
     cur_s = -1;
     thr0 = -1.f;
     pf_tau_s = -1;
+    win0 = 0.f;
     reset();
   }
   __device__ void unit(int s, int t) {
@@ -159,8 +173,10 @@ struct EpiTop8 {
       cur_s = s;
       reset();
       thr0 = pf_tau_s == s ? pf_tau : load_tau(s);
+      win0 = pf_tau_s == s ? pf_win : load_win(s);
       pf_tau_s = s + ws.tc_cl;  // the next signal tile of this CTA's range, if any
       pf_tau = load_tau(s + ws.tc_cl);
+      pf_win = load_win(s + ws.tc_cl);
     }
     const float4 v = pf_t == t ? pf : load_scales(t);
     __syncwarp();  // every lane has finished with the previous unit's scales
@@ -240,6 +256,12 @@ struct EpiTop8 {
         if ((sv[j] & ~31u) == (mbits & ~31u)) jb = j;
       lbk = (mbits & ~31u) | static_cast<uint32_t>(31 - jb);
       lbi = nb + jb;
+    }
+    // the window below the running best (lower bounds of scores this thread has seen, this
+    // chunk's largest included), rounded down
+    if (win0 > 0.f) {
+      const float best = fmaxf(ts[0], __uint_as_float(lbk & ~31u));
+      thr = fmaxf(thr, best * (1.f - 0x1p-20f) - win0);
     }
     // x > thr for x, thr >= 0 exactly when bits(x) > bits(thr); a negative thr (an unfilled list
     // with no pruning threshold) passes every column

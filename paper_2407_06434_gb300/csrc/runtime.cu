@@ -128,6 +128,7 @@ Ws solve_ws(const omp_handle_s* h, bool stats) {
     w.rescore_eps = 0.f;
     w.tau = nullptr;
     w.tau_pos = nullptr;
+    w.win_pos = nullptr;
     w.ea = nullptr;
   }
   return w;
@@ -416,7 +417,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
   const bool want_tau = ws.prec == OMP_PREC_BF16 ||
                         (ws.prec == OMP_PREC_FP8_E4M3 && update_default_warps(ws.Mp) == 1);
   if (want_tau && ws.rescore_eps > 0.f && ws.Smax <= kTauSmax)
-    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) &&
+    ok = ok && dalloc(h, &ws.tau, Bm) && dalloc(h, &ws.tau_pos, Bp) && dalloc(h, &ws.win_pos, Bp) &&
          (ws.prec != OMP_PREC_FP8_E4M3 || dalloc(h, &ws.ea, 1));
   ok = ok && dalloc(h, &ws.live[0], Bm) && dalloc(h, &ws.live[1], Bm);
   ok = ok && dalloc(h, &ws.livek[0], Bm) && dalloc(h, &ws.livek[1], Bm);
@@ -443,6 +444,7 @@ omp_status omp_create(const omp_desc* desc, omp_handle* out) {
                  (!h->cand2_buf || cudaMemset(h->cand2_buf, 0, Bm * sizeof(unsigned long long)) == cudaSuccess) &&
                  (!ws.tau || cudaMemset(ws.tau, 0xff, Bm * sizeof(TauRec)) == cudaSuccess) &&
                  (!ws.tau_pos || cudaMemset(ws.tau_pos, 0, Bp * sizeof(float)) == cudaSuccess) &&
+                 (!ws.win_pos || cudaMemset(ws.win_pos, 0, Bp * sizeof(float)) == cudaSuccess) &&
                  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) == cudaSuccess &&
                  configure_update_kernels(ws) == cudaSuccess;

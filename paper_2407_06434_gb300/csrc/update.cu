@@ -151,25 +151,38 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (r < 0) continue;
     const int dest = before + r;
     const int id = in[p0 + i];
-    // the threshold the update kernel of step j - 1 wrote for this signal, for the correlation
-    // (FP8: in the units of the scores, which leave out the row's scale)
-    float tau = 0.f;
-    if (ws.tau_pos && j > 0) {
-      const TauRec t = ws.tau[id];
-      tau = t.step == j && t.tau > 0.f ? t.tau : 0.f;
+    // For the correlation (FP8: in the units of the scores, which leave out the row's scale):
+    // the threshold the update kernel of step j - 1 wrote for this signal, and three score error
+    // bounds at its residual, the same bound and norm the update of step j will use (rounded up)
+    float tau = 0.f, win = 0.f;
+    if (ws.tau_pos) {
+      float eps_j = ws.rescore_eps;
+      if (j > 0) {
+        const TauRec t = ws.tau[id];
+        if (t.step == j) {
+          tau = t.tau > 0.f ? t.tau : 0.f;
+          if (t.eps > 0.f) eps_j = fminf(t.eps, ws.rescore_eps);
+        }
+      }
+      win = 3.f * eps_j * ws.rnorm[id];
+      win = win > 0.f ? win * (1.f + 0x1p-20f) : 0.f;
     }
-    const bool fp8_tau = tau > 0.f && ws.prec == OMP_PREC_FP8_E4M3;
+    const bool fp8_pos = ws.tau_pos && ws.prec == OMP_PREC_FP8_E4M3;
     if (lane == 0) {
       out[dest] = id;
       ws.livek[j & 1][dest] = ws.niter[id];
       ws.cand1[dest] = 0ull;
       if (ws.cand2) ws.cand2[dest] = 0ull;
-      if (ws.tau_pos && !fp8_tau) ws.tau_pos[dest] = tau;
+      if (ws.tau_pos && !fp8_pos) {
+        ws.tau_pos[dest] = tau;
+        ws.win_pos[dest] = win;
+      }
     }
     if (rows_in_place) {
-      if (lane == 0 && fp8_tau) {  // the row's scale was written with it by the update kernel
+      if (lane == 0 && fp8_pos) {  // the row's scale was written with it by the update kernel
         const float sr = ws.sr[j & 1][dest];
         ws.tau_pos[dest] = sr > 0.f ? tau / sr : 0.f;
+        ws.win_pos[dest] = sr > 0.f ? win / sr * (1.f + 0x1p-20f) : 0.f;
       }
       continue;
     }
@@ -211,7 +224,10 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
       const float sr = amax > 0.f ? amax / 448.f : 0.f;
       if (lane == 0) {
         ws.sr[j & 1][dest] = sr;
-        if (fp8_tau) ws.tau_pos[dest] = sr > 0.f ? tau / sr : 0.f;
+        if (fp8_pos) {
+          ws.tau_pos[dest] = sr > 0.f ? tau / sr : 0.f;
+          ws.win_pos[dest] = sr > 0.f ? win / sr * (1.f + 0x1p-20f) : 0.f;
+        }
       }
       uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(ws.Rq[j & 1]) +
                                                   static_cast<size_t>(dest) * ws.Mp);

@@ -14,7 +14,8 @@
 // Roles (64 + 128 EPI_PARTS threads, one CTA per SM):
 //   warp 0 lane 0  TMA producer, NST stages (4 by default; for the correlation 2, 3 or 4, the
 //                  autotuner's choice) of 16 KB (A_op) + 32 KB (B_op), or for a CTA pair 4 or 6
-//                  stages of 16 KB + 16 KB
+//                  stages of 16 KB + 16 KB; with one CTA it issues the first NST stages as soon as
+//                  it has initialised the barriers, before the tensor memory is allocated
 //   warp 1         TMEM allocation (2 x 256 columns); lane 0 issues the MMAs and commits
 //   warps 2..      epilogue, EPI_PARTS warps per TMEM lane quarter (a warp may only read the
 //                  quarter warp % 4), each over EPI_COLS of the unit's 256 columns: tcgen05.ld
@@ -347,6 +348,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars_gen + 8 * (2 * NST + 6));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars_gen + 8 * (2 * NST + 6) + 4);
 
+  const int kelems = KB / (PREC == OMP_PREC_BF16 ? 2 : 1);  // K elements per stage
+  int n_pre = 0;  // one CTA: stages the producer thread issued before the block barrier
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full(s), 1);
@@ -361,6 +364,24 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (CL == 1) {
+      // This thread is the producer: with one CTA it fetches both tensor maps and issues the
+      // first NST stages now, in the producer loop's order, so that they are in flight while
+      // warp 1 allocates the tensor memory and the block meets at the barrier below. (A pair
+      // waits for the cluster barrier: its copies complete on the other CTA's barriers.)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm_a)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm_b)) : "memory");
+      for (int u = u0; u < u1 && n_pre < NST; ++u) {
+        const int sg = u / Tn, t = u - sg * Tn;
+        for (int kc = 0; kc < ktiles && n_pre < NST; ++kc) {
+          const uint32_t dst = base + n_pre * SS;
+          mbar_expect_tx(full(n_pre), SS);
+          tma_load_2d(dst, tm_a, kc * kelems, sg * BM, full(n_pre));
+          tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(n_pre));
+          ++n_pre;
+        }
+      }
+    }
   }
   unsigned long long* peers =
       reinterpret_cast<unsigned long long*>(bars_gen + 256 + EPI_WARPS * EPI_SCRATCH * 4);
@@ -386,7 +407,6 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
   if (CL > 1) cluster_sync();  // no copy or arrival reaches a peer's barriers before their init
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int kelems = KB / (PREC == OMP_PREC_BF16 ? 2 : 1);  // K elements per stage
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ TMA producer
@@ -400,22 +420,26 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tm_a, const CUtenso
       const int sg = u / Tn, t = u - sg * Tn;
       const int s = sg * CL + rank;
       for (int kc = 0; kc < ktiles; ++kc) {
-        if (!mbar_wait(empty(stage), ph ^ 1u, abort_flag, err)) {
-          ok = false;
-          break;
-        }
-        const uint32_t dst = base + stage * SS;
-        if (PAIR) {
-          // both CTAs' copies of the stage complete on the even CTA's full barrier, which
-          // expects the bytes of both
-          if (lead) mbar_expect_tx(full(stage), 2 * SS);
-          const uint32_t fb = cluster_addr(full(stage), 0);
-          tma_load_2d_pair(dst, tm_a, kc * kelems, s * BM, fb);
-          tma_load_2d_pair(dst + SA, tm_b, kc * kelems, t * BN + rank * (BN / 2), fb);
+        if (n_pre > 0) {  // issued before the block barrier (stage n_pre counts up from 0)
+          --n_pre;
         } else {
-          mbar_expect_tx(full(stage), SS);
-          tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
-          tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(stage));
+          if (!mbar_wait(empty(stage), ph ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = base + stage * SS;
+          if (PAIR) {
+            // both CTAs' copies of the stage complete on the even CTA's full barrier, which
+            // expects the bytes of both
+            if (lead) mbar_expect_tx(full(stage), 2 * SS);
+            const uint32_t fb = cluster_addr(full(stage), 0);
+            tma_load_2d_pair(dst, tm_a, kc * kelems, s * BM, fb);
+            tma_load_2d_pair(dst + SA, tm_b, kc * kelems, t * BN + rank * (BN / 2), fb);
+          } else {
+            mbar_expect_tx(full(stage), SS);
+            tma_load_2d(dst, tm_a, kc * kelems, s * BM, full(stage));
+            tma_load_2d(dst + SA, tm_b, kc * kelems, t * BN, full(stage));
+          }
         }
 #pragma unroll
         for (int q = 0; q < NST; ++q)  // static indices keep last_ph in registers

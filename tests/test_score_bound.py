@@ -115,3 +115,37 @@ def test_fp8_subnormal_range_is_covered():
         assert w <= bound
         # the subnormal part alone: (M - 1) errors of 0.49 2^-9 against ||a|| ||r|| ~ 448 sqrt(M)
         assert w > 0.9 * (M - 1) * 0.49 * 2.0 ** -9 / (448.0 * np.sqrt(M))
+
+
+def test_running_best_window_keeps_the_pick_and_the_rescoring_window():
+    """The correlation epilogue drops a column whose quantised score is at or below the best
+    quantised score seen so far, less three bounds eps ||r||. Scanned in the kernel's order
+    (ascending columns, the running best taken over whole 32-column chunks, this chunk's
+    included), with the oracle's BF16 rounding: no dropped column is the exact argmax (lowest
+    index on ties) or lies within the rescoring window, 2 eps ||r|| below the best quantised
+    score. Columns are drawn near the best so that the window is crowded."""
+    M, N = 1024, 4096
+    eps = omp.omp_score_error_bound(BF16, M)
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        A = rng.standard_normal((N, M)).astype(np.float32)
+        r = rng.standard_normal(M).astype(np.float32)
+        # crowd the top: columns that are the residual's direction plus noise of varying size,
+        # so that many quantised scores fall within a few bounds of each other
+        near = rng.choice(N, 64, replace=False)
+        A[near] = (r[None, :] * rng.uniform(0.9, 1.0, (64, 1)) +
+                   rng.standard_normal((64, M)) * rng.uniform(0.0, 0.05 * (trial + 1), (64, 1))).astype(np.float32)
+        nrm = np.linalg.norm(A.astype(np.float64), axis=1)
+        Aq = quant.bf16_round(A).astype(np.float64)
+        rq = quant.bf16_round(r).astype(np.float64)
+        exact = np.abs(A.astype(np.float64) @ r.astype(np.float64)) / nrm
+        qsc = np.abs(Aq @ rq) / nrm
+        rn = float(np.linalg.norm(r.astype(np.float64)))
+        win3 = 3.0 * eps * rn
+        chunk_best = np.maximum.accumulate(qsc.reshape(-1, 32).max(axis=1))
+        dropped = qsc <= np.repeat(chunk_best, 32) - win3
+        pick = int(np.argmax(exact))                  # lowest index among equal maxima
+        assert not dropped[pick]
+        in_window = qsc >= qsc.max() - 2.0 * eps * rn
+        assert not np.any(dropped & in_window)
+        assert dropped.sum() > N // 2                 # the window does prune

@@ -40,6 +40,7 @@ METRIC = "OMP signals/s, chosen form vs plain FP32 on same GB300 at matched supp
 # entry is removed whenever its kernel changes.
 L2_RESIDENT_BYTES = 64 << 20   # an FP32 dictionary up to half the 129 MB L2 stays resident
 MEASURED_TRAFFIC = {
+    ("gaussian_1024x8192_s32_b4096", "bf16", "correlate"): 25316864.0,
     ("gaussian_1024x8192_s32_b4096", "bf16", "update"): 61508864.0,
 }
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}

@@ -53,6 +53,11 @@ def make_training_set(solver_h, A_dev, w, n_signals: int, chunk: int, seed: int 
                       threads: int = 8):
     """Synthesise n_signals training signals on the device and label them with plain OMP.
 
+    The labels are the supports of the dense solve (Alg. 1, no proposal) of the handle given. On
+    a BF16 or FP8 handle the FP32 rescoring makes every pick the FP32 path's (the GPU tests assert
+    bit-identical supports), so the labels are those of plain FP32 OMP at the quantised form's
+    cost.
+
     Returns (Y (n x M), labels (n x S int32), drops (n x S float32)) as device tensors."""
     import torch
     from workloads import gen

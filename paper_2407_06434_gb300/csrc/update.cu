@@ -113,6 +113,24 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (blockIdx.x == 0 && tid == 0) ws.cnt[j + 1] = 0;
     return;
   }
+  // The signals at this warp's two positions and their records (iteration count, threshold
+  // record, residual norm) do not depend on the kept flags, so their loads go out first and land
+  // while the flags are counted
+  static_assert(kCompactChunk == 16, "two positions per warp of eight");
+  int pid[2], pnk[2];
+  float prn[2];
+  TauRec ptr[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int p = p0 + warp + 8 * m;
+    pid[m] = p < Lin ? in[p] : 0;
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    pnk[m] = ws.niter[pid[m]];
+    prn[m] = ws.tau_pos ? ws.rnorm[pid[m]] : 0.f;
+    ptr[m] = ws.tau_pos && j > 0 ? ws.tau[pid[m]] : TauRec{0.f, 0.f, -1, 0};
+  }
   // kept flags before p0 (a multiple of 16; flags are 0 or 1 bytes, so a word's bit count is
   // its number of kept positions)
   int c = 0;
@@ -146,11 +164,13 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (p0 + i < Lin && dest_s[i] != i) keep_all = 0;
   const bool rows_in_place = reuse && ws.upd_w == 1 && ws.prec != OMP_PREC_FP32 && before == p0 &&
                              keep_all;
-  for (int i = warp; i < kCompactChunk; i += 8) {
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int i = warp + 8 * m;
     const int r = dest_s[i];
     if (r < 0) continue;
     const int dest = before + r;
-    const int id = in[p0 + i];
+    const int id = pid[m];
     // For the correlation (FP8: in the units of the scores, which leave out the row's scale):
     // the threshold the update kernel of step j - 1 wrote for this signal, and three score error
     // bounds at its residual, the same bound and norm the update of step j will use (rounded up)
@@ -158,19 +178,19 @@ __global__ void __launch_bounds__(256) compact_kernel(Ws ws, int j, int S, int r
     if (ws.tau_pos) {
       float eps_j = ws.rescore_eps;
       if (j > 0) {
-        const TauRec t = ws.tau[id];
+        const TauRec t = ptr[m];
         if (t.step == j) {
           tau = t.tau > 0.f ? t.tau : 0.f;
           if (t.eps > 0.f) eps_j = fminf(t.eps, ws.rescore_eps);
         }
       }
-      win = 3.f * eps_j * ws.rnorm[id];
+      win = 3.f * eps_j * prn[m];
       win = win > 0.f ? win * (1.f + 0x1p-20f) : 0.f;
     }
     const bool fp8_pos = ws.tau_pos && ws.prec == OMP_PREC_FP8_E4M3;
     if (lane == 0) {
       out[dest] = id;
-      ws.livek[j & 1][dest] = ws.niter[id];
+      ws.livek[j & 1][dest] = pnk[m];
       ws.cand1[dest] = 0ull;
       if (ws.cand2) ws.cand2[dest] = 0ull;
       if (ws.tau_pos && !fp8_pos) {

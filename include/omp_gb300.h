@@ -270,7 +270,7 @@ omp_status omp_read_bandwidth_probe(const void* buf, int64_t bytes, int32_t reps
  * runs the OMP iteration restricted to the proposed atoms (the projections of Sec. 2.3's D matrix
  * restricted to the candidates) and sends every signal whose step fails the residual-drop check
  * b_k^2 / ||r_{k-1}||^2 >= tau_k back to the full correlation from that step on.
- * The paper has no learned component; plain OMP remains the judge of its results.
+ * The paper has no learned component; its results are checked against plain OMP's.
  * ------------------------------------------------------------------------------------------ */
 typedef struct omp_proposal_s* omp_proposal;
 

@@ -137,9 +137,11 @@ struct EpiTop8 {
   }
   // Three score error bounds at the row's residual (written per live position by the
   // compaction, in the units of the scores): a column whose score is that far below the best
-  // score the row has shown so far has an FP32 score more than two bounds below the best FP32
-  // score, so it can be neither the pick nor a rescoring candidate that changes it. This prunes
-  // where no previous step left a threshold (the first step) as well as past the best column.
+  // score the row has shown so far is more than two bounds below the row's final best score,
+  // outside the window of the FP32 rescoring, and its FP32 score is at least one bound below the
+  // best FP32 score, so it can be neither the pick nor a rescoring candidate that changes it.
+  // This prunes where no previous step left a threshold (the first step) as well as past the
+  // best column.
   __device__ float load_win(int s) const {
     const int p = s * BM + row;
     if (!ws.win_pos || p >= L) return 0.f;
